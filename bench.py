@@ -1,0 +1,366 @@
+#!/usr/bin/env python3
+"""Throughput of the parallel-tempering hot path on GB300.
+
+One step = one update cycle of every replica of every chain of the workload:
+1 heat-bath sweep + 5L/4 overrelaxation sweeps (section IV of Hasenbusch &
+Schaefer), the energy reduction, one tempering update (the exchange mode of
+the workload) and the overlap reduction.  The metric is site updates per
+nanosecond (each sweep updates every site of every replica once), reported
+beside the HBM roofline of the dominant kernel (the overrelaxation half
+sweep).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+                  [--exchange plain|decimation|coolheat] [--impl ours|reference]
+
+Under torchrun every rank runs its own disorder samples (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1006_4247_gb300 import workloads as W  # noqa: E402
+
+HBM_FALLBACK_GBS = 6800.0
+L2_BYTES = 129e6
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--workload", default="L16_R24_S64")
+    p.add_argument("--exchange", default=None)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return HBM_FALLBACK_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("sweep.cu", "pt_device.cuh", "pt_types.h", "kernels.h"):
+        with open(os.path.join(ROOT, "paper_1006_4247_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload, precision):
+    """DRAM bytes per launch of the OR half sweep from the committed ncu summary,
+    if it was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        d = json.load(fh)
+    e = d.get(f"{workload}:{precision}")
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return float(e["dram_bytes_per_launch"])
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def workload_of(args, rank):
+    w = W.WORKLOADS[args.workload]()
+    if args.exchange:
+        w.exchange = args.exchange
+    w.j_seed0 += 100000 * rank
+    return w
+
+
+def updates_per_step(w):
+    return sum(w.n_copies * nt * L ** 3 for L, nt in zip(w.L, w.n_replicas)) * (w.n_hb + w.n_or)
+
+
+def eps_array(w):
+    return np.concatenate([np.full(nt - 1, w.eps, np.float32) for nt in w.n_replicas])
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline leg and --impl reference)
+# ---------------------------------------------------------------------------
+def oracle_cycle_rate(w, budget_s=12.0, max_cycles=None):
+    """Site updates/ns of the oracle on one sample of the workload, single
+    thread, as it stands."""
+    import oracle
+    oracle.build()
+    L, NT = w.L[0], w.n_replicas[0]
+    J = W.couplings(L, w.j_seed0).astype(np.float64)
+    B = W.linear_betas(NT, w.beta_min, w.beta_max)
+    run = oracle.Run(L, J, B, n_copies=w.n_copies, seed=1, eps=w.eps)
+    mode = {"plain": 0, "decimation": 1, "coolheat": 2}[w.exchange]
+    per_cycle = w.n_copies * NT * L ** 3 * (w.n_hb + w.n_or)
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        run.cycles(1, w.n_hb, w.n_or, mode, record=False)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or (max_cycles and n >= max_cycles):
+            break
+    return per_cycle * n / (el * 1e9), n, el
+
+
+def reference_arm(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    w = workload_of(args, 0)
+    import oracle
+    oracle.build()
+    L, NT = w.L[0], w.n_replicas[0]
+    J = W.couplings(L, w.j_seed0).astype(np.float64)
+    B = W.linear_betas(NT, w.beta_min, w.beta_max)
+    run = oracle.Run(L, J, B, n_copies=w.n_copies, seed=1, eps=w.eps)
+    mode = {"plain": 0, "decimation": 1, "coolheat": 2}[w.exchange]
+    for _ in range(args.warmup):
+        run.cycles(1, w.n_hb, w.n_or, mode, record=False)
+    per_step = w.n_copies * NT * L ** 3 * (w.n_hb + w.n_or)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        run.cycles(1, w.n_hb, w.n_or, mode, record=True)
+    el = time.perf_counter() - t0
+    v = per_step * args.steps / (el * 1e9)
+    sample = f"one sample (L={L}, {NT} replicas x {w.n_copies} copies) of {w.name}, one cycle per step"
+    line = {
+        "metric": "site_updates_per_ns", "value": v, "unit": "updates/ns", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "impl": "reference",
+        "config": {"workload": w.name, "L": L, "replicas": NT, "copies": w.n_copies,
+                   "samples": 1, "n_hb": w.n_hb, "n_or": w.n_or, "exchange": w.exchange},
+        "cpu_baseline": {"value": v, "unit": "updates/ns", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "updates/ns", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def ours(args):
+    import torch
+    from paper_1006_4247_gb300 import _build, pt
+
+    rank, local, world = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    _build.build()
+    w = workload_of(args, rank)
+    stream = torch.cuda.current_stream()
+    Js = np.stack(w.couplings())
+    Bs = np.stack(w.betas())
+    eng = pt.Engine(w.L[0], Js, Bs, n_copies=w.n_copies, precision=args.precision, seed=7 + rank,
+                    stream=stream.cuda_stream)
+    eps = eps_array(w)
+    eng.set_params(eps=eps)
+    mode = w.exchange
+
+    def step():
+        eng.sweep(w.n_hb, w.n_or)
+        eng.exchange(mode)
+        eng.measure_device()
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    eng.profile(True)
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    prof_ms, launches = eng.profile_read()
+    eng.profile(False)
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    ups = updates_per_step(w)
+    value = ups * args.steps * world / (ms * 1e6)
+
+    # roofline of the overrelaxation half sweep
+    NT, L, S, C = w.n_replicas[0], w.L[0], w.n_samples, w.n_copies
+    N = L ** 3
+    R = S * C * NT
+    bpe = 4 if args.precision == "fp32" else 8
+    alg_bytes = R * (N // 2) * 9 * bpe + S * 3 * N * 4
+    n_or_launch = launches["or"]
+    or_avg_s = prof_ms["or"] / max(n_or_launch, 1) / 1e3
+    achieved = alg_bytes / or_avg_s / 1e9
+    peak, peak_src = load_peaks()
+    traffic = ncu_traffic(w.name, args.precision)
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": traffic, "kernel": "k_halfsweep<OR>",
+            "peak_source": peak_src, "alg_bytes_per_launch": alg_bytes,
+            "avg_launch_us": or_avg_s * 1e6}
+    share = {k: v / max(sum(prof_ms.values()), 1e-9) for k, v in prof_ms.items()}
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        B_h = torch.from_numpy(Bs.reshape(-1).copy()).pin_memory()
+        E_h = torch.from_numpy(eps.copy()).pin_memory()
+        Hh = torch.empty(R, dtype=torch.float64).pin_memory()
+        Qh = torch.empty(S * NT * 9, dtype=torch.float64).pin_memory()
+        Xh = torch.empty(S * NT, dtype=torch.float64).pin_memory()
+        Bn, En, Hn, Qn, Xn = (t.numpy() for t in (B_h, E_h, Hh, Qh, Xh))
+
+        def e2e_step():
+            eng.set_params(Bn, En)
+            eng.sweep(w.n_hb, w.n_or)
+            eng.exchange(mode)
+            pt.pt_measure(eng.h, Hn, Qn, Xn)
+
+        for _ in range(2):
+            e2e_step()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        barrier()
+        el = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([el], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": ups * args.steps * world / (el * 1e9), "unit": "updates/ns",
+               "h2d_bytes_per_step": int(Bn.nbytes + En.nbytes),
+               "d2h_bytes_per_step": int(Hn.nbytes + Qn.nbytes + Xn.nbytes)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, n, el = oracle_cycle_rate(w)
+        cpu = {"value": v, "unit": "updates/ns", "cores": 1, "kind": "oracle",
+               "sample": f"{n} cycles of one sample (L={L}, {NT} replicas x {C} copies, "
+                         f"1 HB + {w.n_or} OR + {mode}) in {el:.1f} s, single thread"}
+
+    spins_bytes = eng.R * N * 3 * bpe
+    if rank == 0:
+        line = {
+            "metric": "site_updates_per_ns", "value": value, "unit": "updates/ns", "n_gpus": world,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+            "config": {"workload": w.name, "L": L, "samples": S, "replicas": NT, "copies": C,
+                       "n_hb": w.n_hb, "n_or": w.n_or, "exchange": mode, "eps": w.eps,
+                       "precision": args.precision, "parallelism": f"samples sharded x{world}",
+                       "l2": f"inputs larger than L2 ({spins_bytes / 1e6:.0f} MB of spins > 129 MB)"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(sum(launches.values())), "clocks": clk,
+            "kernel_share": share, "kernel_ms": prof_ms, "kernel_launches": launches,
+        }
+        print(json.dumps(line), flush=True)
+    eng.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        ours(args)
+
+
+if __name__ == "__main__":
+    main()

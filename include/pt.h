@@ -1,0 +1,219 @@
+/*
+ * pt.h -- C ABI of the GB300 parallel-tempering engine for the
+ * three-dimensional Heisenberg Edwards-Anderson spin glass.
+ *
+ * Method: M. Hasenbusch and S. Schaefer, "Speeding up parallel tempering
+ * simulations", arXiv:1006.4247.  N replicas of the model at inverse
+ * temperatures beta_1 < ... < beta_N are updated independently (heat bath +
+ * overrelaxation, section III.C) and configurations are exchanged between
+ * neighbouring temperatures (section I, Eq. 1; improved exchanges of sections
+ * III.A and III.B).  Observables are the energy and the overlap (section II).
+ *
+ * Model (section I): periodic L x L x L simple-cubic lattice, N = L^3 sites,
+ * unit three-component spins s_x, H = - sum_<xy> J_xy s_x . s_y.
+ *
+ * Conventions used throughout this header
+ *   site x = i + L*(j + L*k); colour c(x) = (i + j + k) mod 2 ("black" = 0);
+ *   bond (x, mu) joins x and x + e_mu (periodic) and carries J[mu][x];
+ *   a chain is (sample, copy); the two copies of a sample are independent
+ *   Markov chains used for the overlap (section II);
+ *   "replica" b (0 <= b < n_replicas) is the inverse-temperature index, betas
+ *   strictly increasing with b;
+ *   host arrays are C-contiguous and caller-owned; the library copies what it
+ *   needs and never keeps a host pointer;
+ *   device memory belongs to the handle (or to the allocator callback) and is
+ *   released by pt_destroy.
+ *
+ * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), counter
+ * based, no stored state:
+ *   key = (seed_lo32, seed_hi32 XOR sample)
+ *   ctr = (c0, c1, step_lo32, (purpose << 24) | (step_hi32 & 0xFFFFFF))
+ *   purpose 0 heat bath (c0 = x, c1 = copy*n_replicas + b),
+ *           1 exchange uniform (c0 = pair index, c1 = copy),
+ *           2 decimation re-insertion (c0 = x, c1 = copy*n_replicas + b),
+ *           3 decimation first colour (c0 = 0, c1 = copy),
+ *           4 initial spins (c0 = x, c1 = copy*n_replicas + b, step 0).
+ *   The step counter advances by one per half sweep (pt_sweep) and by one per
+ *   pt_exchange call; it is shared by all chains.
+ *
+ * Errors: every call returns a pt_status and never aborts; pt_last_error()
+ * describes the last failure of the calling thread.  A failed call leaves the
+ * handle usable, except after PT_ERR_CUDA caused by a sticky CUDA error.
+ *
+ * Ordering: calls that only enqueue device work (pt_sweep, pt_exchange,
+ * pt_set_rng_step) return before the work completes; calls that return host
+ * data (pt_measure, pt_get_stats, pt_get_spins, pt_save) synchronise the
+ * engine's stream first.
+ */
+#ifndef PT_H
+#define PT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pt_engine *pt_handle;
+
+typedef enum {
+    PT_OK = 0,
+    PT_ERR_ARG = -1,      /* invalid argument (NULL, size, range, non-finite) */
+    PT_ERR_ODD_L = -2,    /* L odd or < 2: the checkerboard needs a bipartite lattice */
+    PT_ERR_EPS = -3,      /* cooling parameter makes the elementary step non-invertible */
+    PT_ERR_CUDA = -4,     /* a CUDA call failed (text in pt_last_error) */
+    PT_ERR_TIMEOUT = -5,  /* a bounded device-side wait gave up */
+    PT_ERR_STATE = -6,    /* call not valid in the handle's state (e.g. overlap with 1 copy) */
+    PT_ERR_NOMEM = -7     /* device or host allocation failed */
+} pt_status;
+
+typedef enum {
+    PT_PLAIN = 0,       /* standard swap, section I Eq. 1 */
+    PT_DECIMATION = 1,  /* decimation swap, section III.A Eq. aswap */
+    PT_COOLHEAT = 2     /* cooling/heating swap, section III.B */
+} pt_mode;
+
+typedef enum { PT_FP32 = 0, PT_FP64 = 1 } pt_precision;
+typedef enum { PT_START_RANDOM = 0, PT_START_ORDERED = 1 } pt_start;
+
+/* Optional device allocator (for example a framework's caching allocator).
+ * alloc returns a device pointer aligned to at least 256 bytes or NULL. */
+typedef void *(*pt_alloc_fn)(size_t bytes, void *ctx);
+typedef void (*pt_free_fn)(void *ptr, void *ctx);
+
+typedef struct {
+    int n_samples;        /* disorder samples (independent J sets), >= 1 */
+    int n_copies;         /* 1 or 2 chains per sample (2 needed for the overlap) */
+    int precision;        /* pt_precision of the spins and sweep arithmetic */
+    uint64_t seed;        /* Philox seed */
+    int start;            /* pt_start: uniform on the sphere, or all (1,0,0)
+                             as in the equilibration study of section IV.C */
+    void *stream;         /* cudaStream_t for all device work; NULL = legacy stream */
+    pt_alloc_fn alloc;    /* NULL: cudaMalloc */
+    pt_free_fn free;      /* NULL: cudaFree */
+    void *alloc_ctx;
+} pt_options;
+
+/* Fill *opt with defaults: 1 sample, 2 copies, FP32, seed 0, random start,
+ * NULL stream, cudaMalloc. */
+void pt_options_default(pt_options *opt);
+
+/* Create an engine for n_samples samples of one lattice size.
+ *   L          even, >= 2 (PT_ERR_ODD_L otherwise)
+ *   couplings  host float [n_samples][3][L^3], J[mu][x] of bond (x, x + e_mu);
+ *              finite values (section I: Gaussian, zero mean, unit variance)
+ *   betas      host double [n_samples][n_replicas], strictly increasing per
+ *              sample, finite, >= 0
+ *   n_replicas inverse temperatures per copy, >= 2
+ * Spins start as opt->start says; the energies are computed; the
+ * temperature-to-configuration map is the identity; counters are zero. */
+pt_status pt_create(pt_handle *out, int L, const float *couplings,
+                    const double *betas, int n_replicas, const pt_options *opt);
+
+/* Create an engine for samples of different sizes in one batch.
+ *   L[s], n_replicas[s]       per sample (same rules as pt_create)
+ *   couplings[s]              host float [3][L[s]^3]
+ *   betas[s]                  host double [n_replicas[s]]
+ * opt->n_samples is ignored (n_samples is used).  Per-sample arrays returned
+ * by the other calls are concatenated sample by sample (copy-major inside a
+ * sample) instead of being rectangular. */
+pt_status pt_create_batch(pt_handle *out, int n_samples, const int *L,
+                          const int *n_replicas, const float *const *couplings,
+                          const double *const *betas, const pt_options *opt);
+
+/* Enqueue one block of local updates on every replica of every chain:
+ * n_hb heat-bath sweeps, then n_or overrelaxation sweeps (section III.C; the
+ * paper's cycle is 1 + 5L/4, section IV).  Each sweep is a colour-0 half sweep
+ * followed by a colour-1 half sweep (checkerboard order).  n_hb, n_or >= 0. */
+pt_status pt_sweep(pt_handle h, int n_hb, int n_or);
+
+/* Enqueue one tempering update of every chain: pairs (b, b+1) for
+ * b = 0 .. n_replicas-2 in increasing beta, one after the other.
+ *   mode  PT_PLAIN: accept the swap with min[1, exp((b_{i+1}-b_i)(H_{i+1}-H_i))]
+ *         PT_DECIMATION: swap one colour under the decimated action, the
+ *           decimated colour alternating from pair to pair, the first one
+ *           random; on acceptance re-insert the decimated colour by heat bath
+ *         PT_COOLHEAT: propose the cooled configuration of beta_i at beta_{i+1}
+ *           and the heated configuration of beta_{i+1} at beta_i
+ *   eps   host float [n_samples][n_replicas-1] cooling parameters (copied and
+ *         kept for later calls), or NULL to use the stored ones (default 0).
+ *         PT_ERR_EPS if eps * max_x sum_{6 bonds} |J| >= 1 for any pair, or
+ *         eps < 0. */
+pt_status pt_exchange(pt_handle h, pt_mode mode, const float *eps);
+
+/* Synchronise and copy observables to the host (each pointer may be NULL):
+ *   energy  double [n_samples][n_copies][n_replicas]: H of the configuration
+ *           at each beta (H = -sum J s.s; the paper's E is -H/L^3)
+ *   overlap double [n_samples][n_replicas][9]: Q_ab = sum_x s^(0)_a,x s^(1)_b,x
+ *           between the two copies at the same beta (section II)
+ *   chi     double [n_samples][n_replicas]: chi = (1/L^3) sum_ab Q_ab^2
+ * overlap/chi need n_copies == 2 (PT_ERR_STATE otherwise). */
+pt_status pt_measure(pt_handle h, double *energy, double *overlap, double *chi);
+
+/* Enqueue the same reductions as pt_measure without synchronising; results
+ * are written to caller-owned DEVICE buffers of the same layouts (each may be
+ * NULL, in which case the result is computed into the engine's own buffers
+ * only).  For graph capture and for keeping time series on the device. */
+pt_status pt_measure_device(pt_handle h, double *d_energy, double *d_overlap, double *d_chi);
+
+/* Synchronise and copy the exchange bookkeeping (each pointer may be NULL):
+ *   proposals, accepts  int64 [n_samples][n_copies][n_replicas-1] per pair
+ *   round_trips         int64 [n_samples][n_copies]: completed trips
+ *                       beta_0 -> beta_{N-1} -> beta_0 (section IV.B)
+ *   perm                int32 [n_samples][n_copies][n_replicas]: identity
+ *                       (initial replica index) of the configuration now at b */
+pt_status pt_get_stats(pt_handle h, int64_t *proposals, int64_t *accepts,
+                       int64_t *round_trips, int32_t *perm);
+
+/* Copy the configuration at (sample, copy, replica b) to / from the host as
+ * double [L^3][3] in natural site order.  pt_set_spins marks the energies for
+ * recomputation; spins should be unit vectors. */
+pt_status pt_get_spins(pt_handle h, int sample, int copy, int replica, double *xyz);
+pt_status pt_set_spins(pt_handle h, int sample, int copy, int replica, const double *xyz);
+
+/* Replace the inverse temperatures (host double, same layout as at creation)
+ * and/or the cooling parameters (host float [n_samples][n_replicas-1]); either
+ * may be NULL. */
+pt_status pt_set_params(pt_handle h, const double *betas, const float *eps);
+
+/* Set / read the Philox step counter. */
+pt_status pt_set_rng_step(pt_handle h, uint64_t step);
+pt_status pt_get_rng_step(pt_handle h, uint64_t *step);
+
+/* Save / restore the whole chain state (spins, maps, counters, energies,
+ * parameters, step counter) to / from a file.  pt_load needs a handle created
+ * with the same shapes and precision.  Resuming is exact: k cycles, save,
+ * load, k cycles give the same state as 2k cycles. */
+pt_status pt_save(pt_handle h, const char *path);
+pt_status pt_load(pt_handle h, const char *path);
+
+/* Per-kernel-class timing on the engine's stream.
+ * pt_profile(h, 1) starts recording a CUDA event before and after every
+ * kernel launch of the handle (and clears earlier records); pt_profile(h, 0)
+ * stops.  pt_profile_read synchronises and returns, per class, the summed
+ * event time in milliseconds and the number of kernel launches since the
+ * last pt_profile call (launches are counted even while recording is off).
+ * Arrays have PT_KERNEL_KINDS entries; either may be NULL. */
+typedef enum {
+    PT_KERNEL_HB = 0,        /* heat-bath half sweeps */
+    PT_KERNEL_OR = 1,        /* overrelaxation half sweeps */
+    PT_KERNEL_ENERGY = 2,    /* energy reduction and finalisation */
+    PT_KERNEL_EXCHANGE = 3,  /* tempering updates */
+    PT_KERNEL_MEASURE = 4,   /* overlap reduction */
+    PT_KERNEL_OTHER = 5,     /* initial spins, step counter */
+    PT_KERNEL_KINDS = 6
+} pt_kernel_kind;
+pt_status pt_profile(pt_handle h, int enable);
+pt_status pt_profile_read(pt_handle h, double *ms, int64_t *launches);
+
+/* Release all device memory of the handle.  NULL is accepted. */
+pt_status pt_destroy(pt_handle h);
+
+/* Text of the calling thread's last error ("" if none). */
+const char *pt_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PT_H */

@@ -1,0 +1,746 @@
+// engine.cu -- host side of the C ABI declared in include/pt.h: validation,
+// batch descriptors, device memory, launch sequences, observables, checkpoint.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/pt.h"
+#include "kernels.h"
+#include "pt_types.h"
+
+using namespace ptk;
+
+namespace {
+
+thread_local char g_err[1024] = "";
+
+pt_status fail(pt_status st, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+#define CK(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(PT_ERR_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                        __FILE__, __LINE__);                                              \
+    } while (0)
+
+FastDiv make_fastdiv(uint32_t d) {
+    FastDiv f{d, 0u, 0u, 0u};
+    if (d <= 1) return f;  // m == 0 flags d == 1
+    uint32_t l = 0;
+    while ((1ull << l) < d) ++l;
+    const unsigned __int128 num = (unsigned __int128)1 << (31 + l);
+    f.m = (uint32_t)((num + d - 1) / d);
+    f.s = l - 1;
+    return f;
+}
+
+constexpr int kMaxNT = 512;  // must match the exchange kernels' shared-memory limit
+
+}  // namespace
+
+struct pt_engine {
+    int S = 0, C = 0;
+    bool fp64 = false;
+    uint64_t seed = 0;
+    int start = 0;
+    cudaStream_t stream = nullptr;
+    pt_alloc_fn alloc = nullptr;
+    pt_free_fn freefn = nullptr;
+    void* actx = nullptr;
+
+    std::vector<int> L, NT;
+    std::vector<SampleDesc> samples;
+    std::vector<ChainDesc> chains;
+    std::vector<int4> reps;
+    std::vector<int2> tiles;
+    std::vector<long long> chain_off;
+    std::vector<float> maxsumJ;       // per sample: max_x sum of |J| over the 6 bonds
+    std::vector<float> eps_host;      // last cooling parameters
+    size_t pool_elems = 0, J_elems = 0;
+    int R = 0, P = 0, T = 0, sumNT = 0, sumEps = 0;
+    bool energy_valid = false;
+    uint64_t step_host = 0;           // mirror of the device step counter
+
+    std::vector<void*> owned;
+    DevBatch d{};
+
+    // per-kernel-class accounting (pt_profile)
+    bool profiling = false;
+    long long launches[PT_KERNEL_KINDS] = {0};
+    struct Rec { int kind; cudaEvent_t a, b; };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> ev_pool;
+    cudaEvent_t ev_get() {
+        if (!ev_pool.empty()) { cudaEvent_t v = ev_pool.back(); ev_pool.pop_back(); return v; }
+        cudaEvent_t v = nullptr;
+        if (cudaEventCreate(&v) != cudaSuccess) return nullptr;
+        return v;
+    }
+
+    size_t esz() const { return fp64 ? sizeof(double) : sizeof(float); }
+
+    pt_status dalloc(void** p, size_t bytes) {
+        bytes = (bytes + 255) & ~(size_t)255;
+        if (bytes == 0) bytes = 256;
+        if (alloc) {
+            *p = alloc(bytes, actx);
+            if (!*p) return fail(PT_ERR_NOMEM, "allocator callback returned NULL for %zu bytes", bytes);
+        } else {
+            cudaError_t e = cudaMalloc(p, bytes);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return fail(e == cudaErrorMemoryAllocation ? PT_ERR_NOMEM : PT_ERR_CUDA,
+                            "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+            }
+        }
+        owned.push_back(*p);
+        return PT_OK;
+    }
+
+    void release() {
+        if (stream) cudaStreamSynchronize(stream); else cudaDeviceSynchronize();
+        for (Rec& r : recs) { ev_pool.push_back(r.a); ev_pool.push_back(r.b); }
+        recs.clear();
+        for (cudaEvent_t v : ev_pool) if (v) cudaEventDestroy(v);
+        ev_pool.clear();
+        for (void* p : owned) {
+            if (freefn) freefn(p, actx);
+            else cudaFree(p);
+        }
+        owned.clear();
+    }
+};
+
+namespace {
+
+template <typename X>
+pt_status upload(pt_engine* e, X** dst, const std::vector<X>& v) {
+    pt_status st = e->dalloc((void**)dst, sizeof(X) * (v.empty() ? 1 : v.size()));
+    if (st != PT_OK) return st;
+    if (!v.empty())
+        CK(cudaMemcpyAsync(*dst, v.data(), sizeof(X) * v.size(), cudaMemcpyHostToDevice, e->stream));
+    return PT_OK;
+}
+
+// Natural order [N][3] <-> colour-split [c][a][h] of one buffer.
+template <typename X>
+void natural_to_split(int L, const double* xyz, X* buf) {
+    const int N = L * L * L, half = N / 2, hL = L / 2;
+    for (int x = 0; x < N; ++x) {
+        const int i = x % L, j = (x / L) % L, k = x / (L * L);
+        const int c = (i + j + k) & 1;
+        const int h = (i >> 1) + hL * (j + L * k);
+        for (int a = 0; a < 3; ++a) buf[(size_t)c * 3 * half + (size_t)a * half + h] = (X)xyz[3 * x + a];
+    }
+}
+
+template <typename X>
+void split_to_natural(int L, const X* buf, double* xyz) {
+    const int N = L * L * L, half = N / 2, hL = L / 2;
+    for (int x = 0; x < N; ++x) {
+        const int i = x % L, j = (x / L) % L, k = x / (L * L);
+        const int c = (i + j + k) & 1;
+        const int h = (i >> 1) + hL * (j + L * k);
+        for (int a = 0; a < 3; ++a) xyz[3 * x + a] = (double)buf[(size_t)c * 3 * half + (size_t)a * half + h];
+    }
+}
+
+// Run a launcher, count its kernels under `kind` and, while profiling,
+// bracket it with events on the engine's stream.
+template <class F>
+pt_status run(pt_engine* e, int kind, int n_kernels, F&& launcher) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (e->profiling) {
+        a = e->ev_get();
+        b = e->ev_get();
+        if (!a || !b) return fail(PT_ERR_CUDA, "cudaEventCreate failed");
+        CK(cudaEventRecord(a, e->stream));
+    }
+    CK(launcher());
+    e->launches[kind] += n_kernels;
+    if (e->profiling) {
+        CK(cudaEventRecord(b, e->stream));
+        e->recs.push_back({kind, a, b});
+    }
+    return PT_OK;
+}
+
+#define RUN(kind, n, expr)                                               \
+    do {                                                                 \
+        pt_status st_ = run(e, kind, n, [&]() { return (expr); });       \
+        if (st_ != PT_OK) return st_;                                    \
+    } while (0)
+
+pt_status compute_energy(pt_engine* e) {
+    RUN(PT_KERNEL_ENERGY, 1, launch_energy(e->d, e->fp64, e->stream));
+    RUN(PT_KERNEL_ENERGY, 1, launch_energy_finalize(e->d, e->stream));
+    e->energy_valid = true;
+    return PT_OK;
+}
+
+pt_status create_impl(pt_handle* out, int n_samples, const int* Ls, const int* NTs,
+                      const float* const* Js, const double* const* betas, const pt_options* optp) {
+    if (!out) return fail(PT_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    pt_options opt;
+    pt_options_default(&opt);
+    if (optp) opt = *optp;
+    if (n_samples < 1) return fail(PT_ERR_ARG, "n_samples must be >= 1 (got %d)", n_samples);
+    if (opt.n_copies != 1 && opt.n_copies != 2) return fail(PT_ERR_ARG, "n_copies must be 1 or 2");
+    if (opt.precision != PT_FP32 && opt.precision != PT_FP64) return fail(PT_ERR_ARG, "bad precision");
+    if (opt.start != PT_START_RANDOM && opt.start != PT_START_ORDERED) return fail(PT_ERR_ARG, "bad start");
+    if ((opt.alloc == nullptr) != (opt.free == nullptr)) return fail(PT_ERR_ARG, "alloc and free must be given together");
+    if (!Ls || !NTs || !Js || !betas) return fail(PT_ERR_ARG, "NULL per-sample array");
+    for (int s = 0; s < n_samples; ++s) {
+        const int L = Ls[s];
+        if (L < 2 || (L & 1)) return fail(PT_ERR_ODD_L, "sample %d: L = %d must be even and >= 2", s, L);
+        if (L > 1024 || (long long)L * L * L >= (1LL << 30)) return fail(PT_ERR_ARG, "sample %d: L = %d too large", s, L);
+        if (NTs[s] < 2 || NTs[s] > kMaxNT) return fail(PT_ERR_ARG, "sample %d: n_replicas = %d outside [2, %d]", s, NTs[s], kMaxNT);
+        if (!Js[s] || !betas[s]) return fail(PT_ERR_ARG, "sample %d: NULL couplings or betas", s);
+        for (int b = 0; b < NTs[s]; ++b) {
+            const double v = betas[s][b];
+            if (!std::isfinite(v) || v < 0.0) return fail(PT_ERR_ARG, "sample %d: beta[%d] = %g invalid", s, b, v);
+            if (b > 0 && !(v > betas[s][b - 1])) return fail(PT_ERR_ARG, "sample %d: betas not strictly increasing at %d", s, b);
+        }
+        const long long n3 = 3LL * L * L * L;
+        for (long long n = 0; n < n3; ++n)
+            if (!std::isfinite(Js[s][n])) return fail(PT_ERR_ARG, "sample %d: coupling %lld not finite", s, n);
+    }
+
+    pt_engine* e = new (std::nothrow) pt_engine();
+    if (!e) return fail(PT_ERR_NOMEM, "host allocation failed");
+    e->S = n_samples;
+    e->C = opt.n_copies;
+    e->fp64 = opt.precision == PT_FP64;
+    e->seed = opt.seed;
+    e->start = opt.start;
+    e->stream = (cudaStream_t)opt.stream;
+    e->alloc = opt.alloc;
+    e->freefn = opt.free;
+    e->actx = opt.alloc_ctx;
+    e->L.assign(Ls, Ls + n_samples);
+    e->NT.assign(NTs, NTs + n_samples);
+
+    // ---- descriptors ------------------------------------------------------
+    long long J_off = 0, pool = 0;
+    int beta_off = 0, eps_off = 0, r = 0, t = 0, pair = 0;
+    std::vector<float> Jsplit;
+    std::vector<double> beta_all;
+    for (int s = 0; s < n_samples; ++s) {
+        const int L = Ls[s], NT = NTs[s], N = L * L * L, half = N / 2, hL = L / 2;
+        SampleDesc sd{};
+        sd.L = L; sd.hL = hL; sd.half = half; sd.NT = NT;
+        sd.div_hL = make_fastdiv((uint32_t)hL);
+        sd.div_L = make_fastdiv((uint32_t)L);
+        sd.J_off = J_off;
+        sd.beta_off = beta_off;
+        sd.eps_off = eps_off;
+        sd.chain0 = (int)e->chains.size();
+        sd.r0 = r;
+        sd.tile0 = t;
+        sd.tiles_per_rep = (half + TILE - 1) / TILE;
+        // colour-split forward couplings and the invertibility bound
+        Jsplit.resize((size_t)(J_off + 3LL * N));
+        const float* J = Js[s];
+        float mx = 0.f;
+        for (int x = 0; x < N; ++x) {
+            const int i = x % L, j = (x / L) % L, k = x / (L * L);
+            const int c = (i + j + k) & 1;
+            const int h = (i >> 1) + hL * (j + L * k);
+            const int xm[3] = {((i + L - 1) % L) + L * (j + L * k), i + L * (((j + L - 1) % L) + L * k),
+                               i + L * (j + L * ((k + L - 1) % L))};
+            float sum = 0.f;
+            for (int mu = 0; mu < 3; ++mu) {
+                Jsplit[(size_t)J_off + (size_t)c * 3 * half + (size_t)mu * half + h] = J[(size_t)mu * N + x];
+                sum += std::fabs(J[(size_t)mu * N + x]) + std::fabs(J[(size_t)mu * N + xm[mu]]);
+            }
+            mx = std::max(mx, sum);
+        }
+        e->maxsumJ.push_back(mx);
+        for (int b = 0; b < NT; ++b) beta_all.push_back(betas[s][b]);
+        for (int c = 0; c < e->C; ++c) {
+            const int ch = (int)e->chains.size();
+            e->chains.push_back(ChainDesc{s, c, r, pair});
+            e->chain_off.push_back(pool);
+            pool += (long long)(NT + 2) * 3 * N;
+            for (int b = 0; b < NT; ++b) {
+                e->reps.push_back(make_int4(s, ch, b, c * NT + b));
+                for (int k = 0; k < sd.tiles_per_rep; ++k) e->tiles.push_back(make_int2(r, k * TILE));
+                t += sd.tiles_per_rep;
+                ++r;
+            }
+            pair += NT - 1;
+        }
+        e->samples.push_back(sd);
+        J_off += 3LL * N;
+        beta_off += NT;
+        eps_off += NT - 1;
+    }
+    e->R = r;
+    e->T = t;
+    e->P = pair;
+    e->sumNT = beta_off;
+    e->sumEps = eps_off;
+    e->pool_elems = (size_t)pool;
+    e->J_elems = (size_t)J_off;
+    e->eps_host.assign((size_t)eps_off, 0.f);
+
+    // ---- device memory ----------------------------------------------------
+    pt_status st;
+    DevBatch& d = e->d;
+#define TRY(x)                   \
+    do {                         \
+        st = (x);                \
+        if (st != PT_OK) {       \
+            e->release();        \
+            delete e;            \
+            return st;           \
+        }                        \
+    } while (0)
+    TRY(e->dalloc(&d.spins, e->pool_elems * e->esz()));
+    float* dJ; TRY(upload(e, &dJ, Jsplit)); d.J = dJ;
+    double* dB; TRY(upload(e, &dB, beta_all)); d.betas = dB;
+    float* dE; TRY(upload(e, &dE, e->eps_host)); d.eps = dE;
+    std::vector<int> ident(r), zero_i(r, 0), rts(r, 0);
+    for (int q = 0; q < r; ++q) {
+        ident[q] = e->reps[q].z;
+        rts[q] = (e->reps[q].z == 0) ? 1 : 0;  // label 0 starts at b = 0
+    }
+    TRY(upload(e, &d.bufmap, ident));
+    TRY(upload(e, &d.label, ident));
+    TRY(upload(e, &d.rt_state, rts));
+    std::vector<long long> zc((size_t)e->chains.size(), 0), zp((size_t)pair, 0);
+    TRY(upload(e, &d.rt_count, zc));
+    TRY(upload(e, &d.prop, zp));
+    TRY(upload(e, &d.acc, zp));
+    std::vector<double> zH((size_t)r, 0.0);
+    TRY(upload(e, &d.H, zH));
+    std::vector<int2> fb;
+    for (size_t c = 0; c < e->chains.size(); ++c) {
+        const int NT = e->NT[e->chains[c].s];
+        fb.push_back(make_int2(NT, NT + 1));
+    }
+    TRY(upload(e, &d.freebuf, fb));
+    SampleDesc* dS; TRY(upload(e, &dS, e->samples)); d.samples = dS;
+    ChainDesc* dC; TRY(upload(e, &dC, e->chains)); d.chains = dC;
+    int4* dR; TRY(upload(e, &dR, e->reps)); d.reps = dR;
+    int2* dT; TRY(upload(e, &dT, e->tiles)); d.tiles = dT;
+    long long* dO; TRY(upload(e, &dO, e->chain_off)); d.chain_off = dO;
+    std::vector<unsigned long long> z1(1, 0ull);
+    TRY(upload(e, &d.d_step, z1));
+    std::vector<double> zt((size_t)t, 0.0), zt9((size_t)t * 18, 0.0), zq((size_t)e->sumNT * 9, 0.0),
+        zx((size_t)e->sumNT, 0.0);
+    TRY(upload(e, &d.part, zt));
+    TRY(upload(e, &d.part9, zt9));
+    TRY(upload(e, &d.Q, zq));
+    TRY(upload(e, &d.chi, zx));
+#undef TRY
+    d.seed = e->seed;
+    d.n_samples = e->S;
+    d.n_chains = (int)e->chains.size();
+    d.n_reps = r;
+    d.n_tiles = t;
+    d.max_NT = 0;
+    for (int v : e->NT) d.max_NT = std::max(d.max_NT, v);
+
+    st = run(e, PT_KERNEL_OTHER, 1, [&]() { return launch_init_spins(d, e->fp64, e->start, e->stream); });
+    if (st == PT_OK) st = compute_energy(e);
+    if (st == PT_OK) {
+        cudaError_t ce = e->stream ? cudaStreamSynchronize(e->stream) : cudaDeviceSynchronize();
+        if (ce != cudaSuccess) st = fail(PT_ERR_CUDA, "create: %s", cudaGetErrorString(ce));
+    }
+    if (st != PT_OK) {
+        e->release();
+        delete e;
+        return st;
+    }
+    *out = e;
+    return PT_OK;
+}
+
+pt_status sync(pt_engine* e) {
+    CK(e->stream ? cudaStreamSynchronize(e->stream) : cudaDeviceSynchronize());
+    return PT_OK;
+}
+
+pt_status check_eps(pt_engine* e, const float* eps) {
+    for (int s = 0; s < e->S; ++s) {
+        const SampleDesc& sd = e->samples[s];
+        for (int i = 0; i < sd.NT - 1; ++i) {
+            const float v = eps[sd.eps_off + i];
+            if (!std::isfinite(v) || v < 0.f) return fail(PT_ERR_EPS, "sample %d pair %d: eps = %g invalid", s, i, v);
+            if ((double)v * (double)e->maxsumJ[s] >= 1.0)
+                return fail(PT_ERR_EPS, "sample %d pair %d: eps * max sum|J| = %g >= 1 (step not invertible)", s, i,
+                            (double)v * e->maxsumJ[s]);
+        }
+    }
+    return PT_OK;
+}
+
+pt_status locate(pt_engine* e, int sample, int copy, int replica, size_t* elem_off, int* L) {
+    if (sample < 0 || sample >= e->S) return fail(PT_ERR_ARG, "sample %d out of range", sample);
+    if (copy < 0 || copy >= e->C) return fail(PT_ERR_ARG, "copy %d out of range", copy);
+    const SampleDesc& sd = e->samples[sample];
+    if (replica < 0 || replica >= sd.NT) return fail(PT_ERR_ARG, "replica %d out of range", replica);
+    const int ch = sd.chain0 + copy;
+    const int r = e->chains[ch].r0 + replica;
+    int buf = 0;
+    CK(cudaMemcpyAsync(&buf, e->d.bufmap + r, sizeof(int), cudaMemcpyDeviceToHost, e->stream));
+    pt_status st = sync(e);
+    if (st != PT_OK) return st;
+    *elem_off = (size_t)e->chain_off[ch] + (size_t)buf * 6 * sd.half;
+    *L = sd.L;
+    return PT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void pt_options_default(pt_options* opt) {
+    if (!opt) return;
+    std::memset(opt, 0, sizeof *opt);
+    opt->n_samples = 1;
+    opt->n_copies = 2;
+    opt->precision = PT_FP32;
+    opt->seed = 0;
+    opt->start = PT_START_RANDOM;
+}
+
+pt_status pt_create(pt_handle* out, int L, const float* couplings, const double* betas, int n_replicas,
+                    const pt_options* opt) {
+    pt_options o;
+    pt_options_default(&o);
+    if (opt) o = *opt;
+    if (!couplings || !betas) return fail(PT_ERR_ARG, "NULL couplings or betas");
+    if (o.n_samples < 1) return fail(PT_ERR_ARG, "n_samples must be >= 1");
+    const long long N = (long long)L * L * L;
+    std::vector<int> Ls((size_t)o.n_samples, L), NTs((size_t)o.n_samples, n_replicas);
+    std::vector<const float*> Js((size_t)o.n_samples);
+    std::vector<const double*> Bs((size_t)o.n_samples);
+    for (int s = 0; s < o.n_samples; ++s) {
+        Js[s] = couplings + (size_t)s * 3 * (size_t)(N > 0 ? N : 0);
+        Bs[s] = betas + (size_t)s * (size_t)(n_replicas > 0 ? n_replicas : 0);
+    }
+    return create_impl(out, o.n_samples, Ls.data(), NTs.data(), Js.data(), Bs.data(), &o);
+}
+
+pt_status pt_create_batch(pt_handle* out, int n_samples, const int* L, const int* n_replicas,
+                          const float* const* couplings, const double* const* betas, const pt_options* opt) {
+    return create_impl(out, n_samples, L, n_replicas, couplings, betas, opt);
+}
+
+pt_status pt_sweep(pt_handle e, int n_hb, int n_or) {
+    if (!e) return fail(PT_ERR_ARG, "NULL handle");
+    if (n_hb < 0 || n_or < 0) return fail(PT_ERR_ARG, "n_hb, n_or must be >= 0");
+    const int total = 2 * (n_hb + n_or);
+    if (total == 0) return PT_OK;
+    int k = 0;
+    for (int hb = 0; hb < n_hb; ++hb)
+        for (int c = 0; c < 2; ++c, ++k) {
+            const bool last = (k == total - 1);
+            RUN(PT_KERNEL_HB, 1, launch_halfsweep(e->d, e->fp64, 1, last, c, k, e->stream));
+        }
+    for (int o = 0; o < n_or; ++o)
+        for (int c = 0; c < 2; ++c, ++k) {
+            const bool last = (k == total - 1);
+            RUN(PT_KERNEL_OR, 1, launch_halfsweep(e->d, e->fp64, 0, last, c, k, e->stream));
+        }
+    RUN(PT_KERNEL_ENERGY, 1, launch_energy_finalize(e->d, e->stream));
+    RUN(PT_KERNEL_OTHER, 1, launch_advance_step(e->d, total, e->stream));
+    e->step_host += (uint64_t)total;
+    e->energy_valid = true;
+    return PT_OK;
+}
+
+pt_status pt_exchange(pt_handle e, pt_mode mode, const float* eps) {
+    if (!e) return fail(PT_ERR_ARG, "NULL handle");
+    if (mode != PT_PLAIN && mode != PT_DECIMATION && mode != PT_COOLHEAT) return fail(PT_ERR_ARG, "bad mode %d", (int)mode);
+    if (eps) {
+        pt_status st = check_eps(e, eps);
+        if (st != PT_OK) return st;
+        std::memcpy(e->eps_host.data(), eps, sizeof(float) * e->eps_host.size());
+        CK(cudaMemcpyAsync((void*)e->d.eps, e->eps_host.data(), sizeof(float) * e->eps_host.size(),
+                           cudaMemcpyHostToDevice, e->stream));
+    } else if (mode == PT_COOLHEAT) {
+        pt_status st = check_eps(e, e->eps_host.data());
+        if (st != PT_OK) return st;
+    }
+    if (!e->energy_valid) {
+        pt_status st = compute_energy(e);
+        if (st != PT_OK) return st;
+    }
+    RUN(PT_KERNEL_EXCHANGE, 1, launch_exchange(e->d, e->fp64, (int)mode, e->stream));
+    RUN(PT_KERNEL_OTHER, 1, launch_advance_step(e->d, 1, e->stream));
+    e->step_host += 1;
+    return PT_OK;
+}
+
+pt_status pt_measure(pt_handle e, double* energy, double* overlap, double* chi) {
+    if (!e) return fail(PT_ERR_ARG, "NULL handle");
+    if ((overlap || chi) && e->C != 2) return fail(PT_ERR_STATE, "overlap needs n_copies == 2");
+    if (!e->energy_valid) {
+        pt_status st = compute_energy(e);
+        if (st != PT_OK) return st;
+    }
+    if (overlap || chi) RUN(PT_KERNEL_MEASURE, 2, launch_overlap(e->d, e->fp64, e->stream));
+    if (energy) CK(cudaMemcpyAsync(energy, e->d.H, sizeof(double) * e->R, cudaMemcpyDeviceToHost, e->stream));
+    if (overlap) CK(cudaMemcpyAsync(overlap, e->d.Q, sizeof(double) * 9 * e->sumNT, cudaMemcpyDeviceToHost, e->stream));
+    if (chi) CK(cudaMemcpyAsync(chi, e->d.chi, sizeof(double) * e->sumNT, cudaMemcpyDeviceToHost, e->stream));
+    return sync(e);
+}
+
+pt_status pt_measure_device(pt_handle e, double* d_energy, double* d_overlap, double* d_chi) {
+    if (!e) return fail(PT_ERR_ARG, "NULL handle");
+    if (e->C != 2 && (d_overlap || d_chi)) return fail(PT_ERR_STATE, "overlap needs n_copies == 2");
+    if (!e->energy_valid) {
+        pt_status st = compute_energy(e);
+        if (st != PT_OK) return st;
+    }
+    if (e->C == 2) RUN(PT_KERNEL_MEASURE, 2, launch_overlap(e->d, e->fp64, e->stream));
+    if (d_energy) CK(cudaMemcpyAsync(d_energy, e->d.H, sizeof(double) * e->R, cudaMemcpyDeviceToDevice, e->stream));
+    if (d_overlap)
+        CK(cudaMemcpyAsync(d_overlap, e->d.Q, sizeof(double) * 9 * e->sumNT, cudaMemcpyDeviceToDevice, e->stream));
+    if (d_chi) CK(cudaMemcpyAsync(d_chi, e->d.chi, sizeof(double) * e->sumNT, cudaMemcpyDeviceToDevice, e->stream));
+    return PT_OK;
+}
+
+pt_status pt_profile(pt_handle e, int enable) {
+    if (!e) return fail(PT_ERR_ARG, "NULL handle");
+    pt_status st = sync(e);
+    if (st != PT_OK) return st;
+    for (auto& r : e->recs) { e->ev_pool.push_back(r.a); e->ev_pool.push_back(r.b); }
+    e->recs.clear();
+    for (int k = 0; k < PT_KERNEL_KINDS; ++k) e->launches[k] = 0;
+    e->profiling = enable != 0;
+    return PT_OK;
+}
+
+pt_status pt_profile_read(pt_handle e, double* ms, int64_t* launches) {
+    if (!e) return fail(PT_ERR_ARG, "NULL handle");
+    pt_status st = sync(e);
+    if (st != PT_OK) return st;
+    double acc[PT_KERNEL_KINDS] = {0};
+    for (auto& r : e->recs) {
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, r.a, r.b));
+        acc[r.kind] += t;
+    }
+    for (int k = 0; k < PT_KERNEL_KINDS; ++k) {
+        if (ms) ms[k] = acc[k];
+        if (launches) launches[k] = e->launches[k];
+    }
+    return PT_OK;
+}
+
+pt_status pt_get_stats(pt_handle e, int64_t* proposals, int64_t* accepts, int64_t* round_trips, int32_t* perm) {
+    if (!e) return fail(PT_ERR_ARG, "NULL handle");
+    if (proposals) CK(cudaMemcpyAsync(proposals, e->d.prop, sizeof(int64_t) * e->P, cudaMemcpyDeviceToHost, e->stream));
+    if (accepts) CK(cudaMemcpyAsync(accepts, e->d.acc, sizeof(int64_t) * e->P, cudaMemcpyDeviceToHost, e->stream));
+    if (round_trips)
+        CK(cudaMemcpyAsync(round_trips, e->d.rt_count, sizeof(int64_t) * e->chains.size(), cudaMemcpyDeviceToHost, e->stream));
+    if (perm) CK(cudaMemcpyAsync(perm, e->d.label, sizeof(int32_t) * e->R, cudaMemcpyDeviceToHost, e->stream));
+    return sync(e);
+}
+
+pt_status pt_get_spins(pt_handle e, int sample, int copy, int replica, double* xyz) {
+    if (!e || !xyz) return fail(PT_ERR_ARG, "NULL argument");
+    size_t off;
+    int L;
+    pt_status st = locate(e, sample, copy, replica, &off, &L);
+    if (st != PT_OK) return st;
+    const size_t n = 3ull * L * L * L;
+    std::vector<char> tmp(n * e->esz());
+    CK(cudaMemcpyAsync(tmp.data(), (char*)e->d.spins + off * e->esz(), n * e->esz(), cudaMemcpyDeviceToHost, e->stream));
+    st = sync(e);
+    if (st != PT_OK) return st;
+    if (e->fp64) split_to_natural(L, (const double*)tmp.data(), xyz);
+    else split_to_natural(L, (const float*)tmp.data(), xyz);
+    return PT_OK;
+}
+
+pt_status pt_set_spins(pt_handle e, int sample, int copy, int replica, const double* xyz) {
+    if (!e || !xyz) return fail(PT_ERR_ARG, "NULL argument");
+    size_t off;
+    int L;
+    pt_status st = locate(e, sample, copy, replica, &off, &L);
+    if (st != PT_OK) return st;
+    const size_t n = 3ull * L * L * L;
+    for (size_t q = 0; q < n; ++q)
+        if (!std::isfinite(xyz[q])) return fail(PT_ERR_ARG, "spin component %zu not finite", q);
+    std::vector<char> tmp(n * e->esz());
+    if (e->fp64) natural_to_split(L, xyz, (double*)tmp.data());
+    else natural_to_split(L, xyz, (float*)tmp.data());
+    CK(cudaMemcpyAsync((char*)e->d.spins + off * e->esz(), tmp.data(), n * e->esz(), cudaMemcpyHostToDevice, e->stream));
+    e->energy_valid = false;
+    return sync(e);
+}
+
+pt_status pt_set_params(pt_handle e, const double* betas, const float* eps) {
+    if (!e) return fail(PT_ERR_ARG, "NULL handle");
+    if (betas) {
+        for (int s = 0; s < e->S; ++s) {
+            const SampleDesc& sd = e->samples[s];
+            for (int b = 0; b < sd.NT; ++b) {
+                const double v = betas[sd.beta_off + b];
+                if (!std::isfinite(v) || v < 0.0) return fail(PT_ERR_ARG, "sample %d: beta[%d] invalid", s, b);
+                if (b > 0 && !(v > betas[sd.beta_off + b - 1])) return fail(PT_ERR_ARG, "sample %d: betas not increasing", s);
+            }
+        }
+        CK(cudaMemcpyAsync((void*)e->d.betas, betas, sizeof(double) * e->sumNT, cudaMemcpyHostToDevice, e->stream));
+    }
+    if (eps) {
+        for (int q = 0; q < e->sumEps; ++q)
+            if (!std::isfinite(eps[q]) || eps[q] < 0.f) return fail(PT_ERR_EPS, "eps[%d] invalid", q);
+        std::memcpy(e->eps_host.data(), eps, sizeof(float) * e->eps_host.size());
+        CK(cudaMemcpyAsync((void*)e->d.eps, e->eps_host.data(), sizeof(float) * e->sumEps, cudaMemcpyHostToDevice,
+                           e->stream));
+    }
+    return sync(e);
+}
+
+pt_status pt_set_rng_step(pt_handle e, uint64_t step) {
+    if (!e) return fail(PT_ERR_ARG, "NULL handle");
+    e->step_host = step;
+    CK(cudaMemcpyAsync(e->d.d_step, &e->step_host, sizeof(uint64_t), cudaMemcpyHostToDevice, e->stream));
+    return sync(e);
+}
+
+pt_status pt_get_rng_step(pt_handle e, uint64_t* step) {
+    if (!e || !step) return fail(PT_ERR_ARG, "NULL argument");
+    unsigned long long v = 0;
+    CK(cudaMemcpyAsync(&v, e->d.d_step, sizeof v, cudaMemcpyDeviceToHost, e->stream));
+    pt_status st = sync(e);
+    if (st != PT_OK) return st;
+    *step = v;
+    return PT_OK;
+}
+
+// Checkpoint file: magic, header of shapes, then the device arrays in a
+// fixed order.
+namespace {
+struct CkptHeader {
+    char magic[8];
+    int version, S, C, fp64, R, P, T, sumNT, sumEps, n_chains, energy_valid;
+    long long pool_elems;
+    unsigned long long seed, step;
+};
+
+struct Blob {
+    void* dev;
+    size_t bytes;
+};
+
+std::vector<Blob> state_blobs(pt_engine* e) {
+    return {{e->d.spins, e->pool_elems * e->esz()},
+            {e->d.bufmap, sizeof(int) * e->R},
+            {e->d.label, sizeof(int) * e->R},
+            {e->d.rt_state, sizeof(int) * e->R},
+            {e->d.rt_count, sizeof(long long) * e->chains.size()},
+            {e->d.prop, sizeof(long long) * e->P},
+            {e->d.acc, sizeof(long long) * e->P},
+            {e->d.H, sizeof(double) * e->R},
+            {e->d.freebuf, sizeof(int2) * e->chains.size()},
+            {(void*)e->d.betas, sizeof(double) * e->sumNT},
+            {(void*)e->d.eps, sizeof(float) * e->sumEps}};
+}
+}  // namespace
+
+pt_status pt_save(pt_handle e, const char* path) {
+    if (!e || !path) return fail(PT_ERR_ARG, "NULL argument");
+    CkptHeader hd{};
+    std::memcpy(hd.magic, "PTGB300", 8);
+    hd.version = 1;
+    hd.S = e->S; hd.C = e->C; hd.fp64 = e->fp64; hd.R = e->R; hd.P = e->P; hd.T = e->T;
+    hd.sumNT = e->sumNT; hd.sumEps = e->sumEps; hd.n_chains = (int)e->chains.size();
+    hd.energy_valid = e->energy_valid;
+    hd.pool_elems = (long long)e->pool_elems;
+    hd.seed = e->seed;
+    unsigned long long step = 0;
+    CK(cudaMemcpyAsync(&step, e->d.d_step, sizeof step, cudaMemcpyDeviceToHost, e->stream));
+    pt_status st = sync(e);
+    if (st != PT_OK) return st;
+    hd.step = step;
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return fail(PT_ERR_ARG, "cannot open %s for writing", path);
+    bool ok = std::fwrite(&hd, sizeof hd, 1, f) == 1;
+    for (const Blob& b : state_blobs(e)) {
+        if (!ok) break;
+        std::vector<char> tmp(b.bytes);
+        cudaError_t ce = cudaMemcpy(tmp.data(), b.dev, b.bytes, cudaMemcpyDeviceToHost);
+        if (ce != cudaSuccess) {
+            std::fclose(f);
+            return fail(PT_ERR_CUDA, "save: %s", cudaGetErrorString(ce));
+        }
+        ok = std::fwrite(tmp.data(), 1, b.bytes, f) == b.bytes;
+    }
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok) return fail(PT_ERR_ARG, "write to %s failed", path);
+    return PT_OK;
+}
+
+pt_status pt_load(pt_handle e, const char* path) {
+    if (!e || !path) return fail(PT_ERR_ARG, "NULL argument");
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(PT_ERR_ARG, "cannot open %s", path);
+    CkptHeader hd{};
+    if (std::fread(&hd, sizeof hd, 1, f) != 1 || std::memcmp(hd.magic, "PTGB300", 8) != 0 || hd.version != 1) {
+        std::fclose(f);
+        return fail(PT_ERR_ARG, "%s is not a checkpoint of this engine", path);
+    }
+    if (hd.S != e->S || hd.C != e->C || hd.fp64 != (int)e->fp64 || hd.R != e->R || hd.P != e->P ||
+        hd.sumNT != e->sumNT || hd.n_chains != (int)e->chains.size() || hd.pool_elems != (long long)e->pool_elems) {
+        std::fclose(f);
+        return fail(PT_ERR_STATE, "checkpoint shapes do not match the handle");
+    }
+    std::vector<std::vector<char>> data;
+    for (const Blob& b : state_blobs(e)) {
+        std::vector<char> tmp(b.bytes);
+        if (std::fread(tmp.data(), 1, b.bytes, f) != b.bytes) {
+            std::fclose(f);
+            return fail(PT_ERR_ARG, "%s is truncated", path);
+        }
+        data.push_back(std::move(tmp));
+    }
+    std::fclose(f);
+    pt_status st = sync(e);
+    if (st != PT_OK) return st;
+    size_t q = 0;
+    for (const Blob& b : state_blobs(e)) {
+        CK(cudaMemcpy(b.dev, data[q].data(), b.bytes, cudaMemcpyHostToDevice));
+        ++q;
+    }
+    // host mirrors of the parameters
+    std::memcpy(e->eps_host.data(), data.back().data(), sizeof(float) * e->sumEps);
+    e->seed = hd.seed;
+    e->d.seed = hd.seed;
+    e->step_host = hd.step;
+    CK(cudaMemcpy(e->d.d_step, &hd.step, sizeof hd.step, cudaMemcpyHostToDevice));
+    e->energy_valid = hd.energy_valid != 0;
+    return PT_OK;
+}
+
+pt_status pt_destroy(pt_handle e) {
+    if (!e) return PT_OK;
+    e->release();
+    delete e;
+    return PT_OK;
+}
+
+const char* pt_last_error(void) { return g_err; }
+
+}  // extern "C"

@@ -1,0 +1,296 @@
+// exchange.cu -- tempering updates of Hasenbusch & Schaefer: the standard
+// swap (section I, Eq. 1), the decimation swap (section III.A, Eq. aswap,
+// appendix A) and the cooling/heating swap (section III.B).
+//
+// One CTA per chain (sample, copy).  The pairs (b, b+1) are visited in
+// increasing beta, each seeing the result of the previous one, so a chain is
+// sequential in b; the lattice work of a pair (decimated sums, re-insertion,
+// cooling and heating sweeps) is spread over the CTA's threads.  The chain's
+// small state (temperature-to-buffer map, labels, energies, round-trip
+// states) is held in shared memory for the whole update.
+#include "kernels.h"
+#include "pt_device.cuh"
+
+namespace ptk {
+
+constexpr int MAX_NT = 512;
+constexpr int EX_THREADS = 512;
+
+struct ChainSmem {
+    int buf[MAX_NT];
+    int lab[MAX_NT];
+    int rts[MAX_NT];
+    double H[MAX_NT];
+    double red[32];
+    int flag;
+    int free0, free1;
+};
+
+__device__ void load_chain(const DevBatch& a, const ChainDesc& cd, int NT, ChainSmem& sm, int ch) {
+    for (int b = threadIdx.x; b < NT; b += blockDim.x) {
+        sm.buf[b] = a.bufmap[cd.r0 + b];
+        sm.lab[b] = a.label[cd.r0 + b];
+        sm.rts[b] = a.rt_state[cd.r0 + b];
+        sm.H[b] = a.H[cd.r0 + b];
+    }
+    if (threadIdx.x == 0) {
+        sm.free0 = a.freebuf[ch].x;
+        sm.free1 = a.freebuf[ch].y;
+    }
+    __syncthreads();
+}
+
+// Round trips (section IV.B): a configuration that was at b = 0, then at
+// b = NT-1, completes a trip when it is back at b = 0.
+__device__ void roundtrip_update(ChainSmem& sm, int NT, long long* count) {
+    const int top = sm.lab[0], bot = sm.lab[NT - 1];
+    if (sm.rts[bot] == 1) sm.rts[bot] = 2;
+    if (sm.rts[top] == 2) {
+        *count += 1;
+        sm.rts[top] = 1;
+    } else if (sm.rts[top] == 0) {
+        sm.rts[top] = 1;
+    }
+}
+
+__device__ void store_chain(const DevBatch& a, const ChainDesc& cd, int NT, ChainSmem& sm, int ch) {
+    __syncthreads();
+    if (threadIdx.x == 0) roundtrip_update(sm, NT, &a.rt_count[ch]);
+    __syncthreads();
+    for (int b = threadIdx.x; b < NT; b += blockDim.x) {
+        a.bufmap[cd.r0 + b] = sm.buf[b];
+        a.label[cd.r0 + b] = sm.lab[b];
+        a.rt_state[cd.r0 + b] = sm.rts[b];
+        a.H[cd.r0 + b] = sm.H[b];
+    }
+    if (threadIdx.x == 0) a.freebuf[ch] = make_int2(sm.free0, sm.free1);
+}
+
+// D(n) = ln I(b2 n) - ln I(b1 n) for |S| = n.  With
+// ln(sinh R / R) = R - ln(2R) + ln(1 - e^{-2R}) (appendix A) the large parts
+// reduce to (b2 - b1) n - ln(b2/b1), which keeps float accuracy; below
+// R = 1/2 the difference is taken directly.
+template <typename T>
+__device__ __forceinline__ T decim_D(T n, T b1, T b2, T db, T lr) {
+    const T R1 = b1 * n, R2 = b2 * n;
+    if (R1 >= (T)0.5)
+        return db * n - lr + M<T>::log1p_(-M<T>::exp_((T)-2 * R2)) - M<T>::log1p_(-M<T>::exp_((T)-2 * R1));
+    return ln_sinhc<T>(R2) - ln_sinhc<T>(R1);
+}
+
+__device__ __forceinline__ bool metropolis(double lnA, double u) { return lnA >= 0.0 || u < exp(lnA); }
+
+// ---------------------------------------------------------------------------
+// Standard swap: Delta = (b_{i+1} - b_i)(H_{i+1} - H_i) in double.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(32) k_exchange_plain(DevBatch a) {
+    __shared__ ChainSmem sm;
+    const int ch = blockIdx.x;
+    const ChainDesc cd = a.chains[ch];
+    const SampleDesc& sd = a.samples[cd.s];
+    const int NT = sd.NT;
+    load_chain(a, cd, NT, sm, ch);
+    if (threadIdx.x == 0) {
+        const unsigned long long step = *a.d_step;
+        const double* beta = a.betas + sd.beta_off;
+        for (int i = 0; i + 1 < NT; ++i) {
+            const double lnA = (beta[i + 1] - beta[i]) * (sm.H[i + 1] - sm.H[i]);
+            const uint4 w = rng_words(a.seed, (uint32_t)cd.s, (uint32_t)i, (uint32_t)cd.copy, step, 1u);
+            a.prop[cd.pair_off + i] += 1;
+            if (metropolis(lnA, u53(w.x, w.y))) {
+                a.acc[cd.pair_off + i] += 1;
+                int t = sm.buf[i]; sm.buf[i] = sm.buf[i + 1]; sm.buf[i + 1] = t;
+                t = sm.lab[i]; sm.lab[i] = sm.lab[i + 1]; sm.lab[i + 1] = t;
+                const double th = sm.H[i]; sm.H[i] = sm.H[i + 1]; sm.H[i + 1] = th;
+            }
+        }
+    }
+    store_chain(a, cd, NT, sm, ch);
+}
+
+// ---------------------------------------------------------------------------
+// Decimation swap.  For pair i the decimated colour is d = (d0 + i) mod 2
+// (d0 from purpose 3).  ln A = sum over decimated x of
+// ln I(b2 S1) - ln I(b1 S1) + ln I(b1 S2) - ln I(b2 S2), S from the kept
+// colour; per-site terms in T, sums in double.  On acceptance the buffers
+// swap temperatures and the decimated colour of both is redrawn by heat bath
+// at its new beta (purpose 2), which also yields the new energies.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(EX_THREADS) k_exchange_decimation(DevBatch a) {
+    __shared__ ChainSmem sm;
+    const int ch = blockIdx.x;
+    const ChainDesc cd = a.chains[ch];
+    const SampleDesc& sd = a.samples[cd.s];
+    const int NT = sd.NT, half = sd.half;
+    load_chain(a, cd, NT, sm, ch);
+    const unsigned long long step = *a.d_step;
+    const double* beta = a.betas + sd.beta_off;
+    T* pool = (T*)a.spins + a.chain_off[ch];
+    const uint4 wd = rng_words(a.seed, (uint32_t)cd.s, 0u, (uint32_t)cd.copy, step, 3u);
+    const int d0 = (int)(wd.x & 1u);
+    for (int i = 0; i + 1 < NT; ++i) {
+        const int d = (d0 + i) & 1;
+        const double b1 = beta[i], b2 = beta[i + 1];
+        const T b1t = (T)b1, b2t = (T)b2;
+        const T* c1 = pool + (long long)sm.buf[i] * (6LL * half);
+        const T* c2 = pool + (long long)sm.buf[i + 1] * (6LL * half);
+        const float* Jd = a.J + sd.J_off + d * 3 * half;
+        const float* Jk = a.J + sd.J_off + (1 - d) * 3 * half;
+        const T dbt = (T)(b2 - b1);
+        const T lr = b1 > 0.0 ? (T)log(b2 / b1) : (T)0;
+        double lnA_part = 0.0;
+        for (int h = threadIdx.x; h < half; h += blockDim.x) {
+            const Site st = site_of(sd, d, h);
+            const V3<T> S1 = local_field<T>(st, half, c1 + (1 - d) * 3 * half, Jd, Jk);
+            const V3<T> S2 = local_field<T>(st, half, c2 + (1 - d) * 3 * half, Jd, Jk);
+            const T na = M<T>::sqrt_(dot(S1, S1)), nb = M<T>::sqrt_(dot(S2, S2));
+            const T term = decim_D<T>(na, b1t, b2t, dbt, lr) - decim_D<T>(nb, b1t, b2t, dbt, lr);
+            lnA_part += (double)term;
+        }
+        const double lnA = block_sum(lnA_part, sm.red);
+        if (threadIdx.x == 0) {
+            const uint4 w = rng_words(a.seed, (uint32_t)cd.s, (uint32_t)i, (uint32_t)cd.copy, step, 1u);
+            a.prop[cd.pair_off + i] += 1;
+            const bool ok = metropolis(lnA, u53(w.x, w.y));
+            sm.flag = ok;
+            if (ok) {
+                a.acc[cd.pair_off + i] += 1;
+                int t = sm.buf[i]; sm.buf[i] = sm.buf[i + 1]; sm.buf[i + 1] = t;
+                t = sm.lab[i]; sm.lab[i] = sm.lab[i + 1]; sm.lab[i + 1] = t;
+            }
+        }
+        __syncthreads();
+        if (sm.flag) {
+            double e1 = 0.0, e2 = 0.0;
+            T* n1 = pool + (long long)sm.buf[i] * (6LL * half);      // now at b1
+            T* n2 = pool + (long long)sm.buf[i + 1] * (6LL * half);  // now at b2
+            const uint32_t id1 = (uint32_t)(cd.copy * NT + i), id2 = id1 + 1u;
+            for (int h = threadIdx.x; h < half; h += blockDim.x) {
+                const Site st = site_of(sd, d, h);
+                const V3<T> S1 = local_field<T>(st, half, n1 + (1 - d) * 3 * half, Jd, Jk);
+                const uint4 w1 = rng_words(a.seed, (uint32_t)cd.s, (uint32_t)st.x, id1, step, 2u);
+                const V3<T> s1 = hb_site<T>(b1t, S1, w1.x, w1.y);
+                st3(n1 + d * 3 * half, half, h, s1);
+                e1 -= (double)dot(s1, S1);
+                const V3<T> S2 = local_field<T>(st, half, n2 + (1 - d) * 3 * half, Jd, Jk);
+                const uint4 w2 = rng_words(a.seed, (uint32_t)cd.s, (uint32_t)st.x, id2, step, 2u);
+                const V3<T> s2 = hb_site<T>(b2t, S2, w2.x, w2.y);
+                st3(n2 + d * 3 * half, half, h, s2);
+                e2 -= (double)dot(s2, S2);
+            }
+            const double E1 = block_sum(e1, sm.red);
+            const double E2 = block_sum(e2, sm.red);
+            if (threadIdx.x == 0) {
+                sm.H[i] = E1;
+                sm.H[i + 1] = E2;
+            }
+        }
+        __syncthreads();
+    }
+    store_chain(a, cd, NT, sm, ch);
+}
+
+// ---------------------------------------------------------------------------
+// Cooling/heating swap of pair (b1 < b2) with configurations s1 (at b1) and
+// s2 (at b2): s1 is cooled (colour 0 then colour 1) into scratch buffer f1
+// and proposed at b2; s2 is heated (colour 1 then colour 0, each the inverse
+// step) into scratch buffer f2 and proposed at b1.  The map is an
+// involution, so
+//   ln A = -b2 H[C s1] - b1 H[C^-1 s2] + b1 H[s1] + b2 H[s2]
+//          + ln det J_C(s1) - ln det J_C(C^-1 s2).
+// On acceptance the scratch buffers take the two temperatures and the old
+// buffers become scratch; nothing is copied.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(EX_THREADS) k_exchange_coolheat(DevBatch a) {
+    __shared__ ChainSmem sm;
+    const int ch = blockIdx.x;
+    const ChainDesc cd = a.chains[ch];
+    const SampleDesc& sd = a.samples[cd.s];
+    const int NT = sd.NT, half = sd.half;
+    load_chain(a, cd, NT, sm, ch);
+    const unsigned long long step = *a.d_step;
+    const double* beta = a.betas + sd.beta_off;
+    T* pool = (T*)a.spins + a.chain_off[ch];
+    const float* J0 = a.J + sd.J_off;
+    const float* J1 = a.J + sd.J_off + 3 * half;
+    const long long rep = 6LL * half;
+    for (int i = 0; i + 1 < NT; ++i) {
+        const double b1 = beta[i], b2 = beta[i + 1];
+        const T eps = (T)a.eps[sd.eps_off + i];
+        const T* s1 = pool + (long long)sm.buf[i] * rep;
+        const T* s2 = pool + (long long)sm.buf[i + 1] * rep;
+        T* f1 = pool + (long long)sm.free0 * rep;
+        T* f2 = pool + (long long)sm.free1 * rep;
+        double lj1 = 0.0, lj2 = 0.0, Hc = 0.0, Hh = 0.0;
+        // phase 1: cool colour 0 of s1 (neighbours: s1 colour 1);
+        //          heat colour 1 of s2 (neighbours: s2 colour 0)
+        for (int h = threadIdx.x; h < half; h += blockDim.x) {
+            const Site st0 = site_of(sd, 0, h);
+            const V3<T> S = local_field<T>(st0, half, s1 + 3 * half, J0, J1);
+            V3<T> s = ld3(s1, half, h);
+            lj1 += (double)cool_site<T>(eps, S, s);
+            st3(f1, half, h, s);
+            const Site st1 = site_of(sd, 1, h);
+            const V3<T> S2 = local_field<T>(st1, half, s2, J1, J0);
+            V3<T> u = ld3(s2 + 3 * half, half, h);
+            lj2 += (double)heat_site<T>(eps, S2, u);
+            st3(f2 + 3 * half, half, h, u);
+        }
+        __syncthreads();
+        // phase 2: cool colour 1 of s1 (neighbours: cooled colour 0 in f1);
+        //          heat colour 0 of s2 (neighbours: heated colour 1 in f2)
+        for (int h = threadIdx.x; h < half; h += blockDim.x) {
+            const Site st1 = site_of(sd, 1, h);
+            const V3<T> S = local_field<T>(st1, half, f1, J1, J0);
+            V3<T> s = ld3(s1 + 3 * half, half, h);
+            lj1 += (double)cool_site<T>(eps, S, s);
+            st3(f1 + 3 * half, half, h, s);
+            Hc -= (double)dot(s, S);
+            const Site st0 = site_of(sd, 0, h);
+            const V3<T> S2 = local_field<T>(st0, half, f2 + 3 * half, J0, J1);
+            V3<T> u = ld3(s2, half, h);
+            lj2 += (double)heat_site<T>(eps, S2, u);
+            st3(f2, half, h, u);
+            Hh -= (double)dot(u, S2);
+        }
+        const double LJ1 = block_sum(lj1, sm.red);
+        const double LJ2 = block_sum(lj2, sm.red);
+        const double HC = block_sum(Hc, sm.red);
+        const double HH = block_sum(Hh, sm.red);
+        if (threadIdx.x == 0) {
+            const double lnA = -b2 * HC - b1 * HH + b1 * sm.H[i] + b2 * sm.H[i + 1] + LJ1 - LJ2;
+            const uint4 w = rng_words(a.seed, (uint32_t)cd.s, (uint32_t)i, (uint32_t)cd.copy, step, 1u);
+            a.prop[cd.pair_off + i] += 1;
+            if (metropolis(lnA, u53(w.x, w.y))) {
+                a.acc[cd.pair_off + i] += 1;
+                const int o1 = sm.buf[i], o2 = sm.buf[i + 1];
+                sm.buf[i] = sm.free1;      // C^-1(s2) at b1
+                sm.buf[i + 1] = sm.free0;  // C(s1) at b2
+                sm.free0 = o1;
+                sm.free1 = o2;
+                sm.H[i] = HH;
+                sm.H[i + 1] = HC;
+                const int t = sm.lab[i]; sm.lab[i] = sm.lab[i + 1]; sm.lab[i + 1] = t;
+            }
+        }
+        __syncthreads();
+    }
+    store_chain(a, cd, NT, sm, ch);
+}
+
+cudaError_t launch_exchange(const DevBatch& b, bool fp64, int mode, cudaStream_t st) {
+    if (mode == 0) {
+        k_exchange_plain<<<b.n_chains, 32, 0, st>>>(b);
+    } else if (mode == 1) {
+        if (fp64) k_exchange_decimation<double><<<b.n_chains, EX_THREADS, 0, st>>>(b);
+        else k_exchange_decimation<float><<<b.n_chains, EX_THREADS, 0, st>>>(b);
+    } else {
+        if (fp64) k_exchange_coolheat<double><<<b.n_chains, EX_THREADS, 0, st>>>(b);
+        else k_exchange_coolheat<float><<<b.n_chains, EX_THREADS, 0, st>>>(b);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace ptk

@@ -1,0 +1,50 @@
+// kernels.h -- host-side launchers of the engine's CUDA kernels (internal).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pt_types.h"
+
+namespace ptk {
+
+// Everything a kernel may need about the batch; pointers are device pointers.
+struct DevBatch {
+    void* spins;                    // float or double pool (see pt_types.h)
+    const float* J;                 // colour-split forward couplings
+    const double* betas;            // [sum NT]
+    const float* eps;               // [sum (NT - 1)]
+    int* bufmap;                    // [R] physical buffer of replica r
+    int* label;                     // [R] identity of the configuration at r
+    int* rt_state;                  // [R] round-trip state, indexed r0 + label
+    long long* rt_count;            // [chains]
+    long long* prop;                // [pairs]
+    long long* acc;                 // [pairs]
+    double* H;                      // [R] energy of the configuration at r
+    int2* freebuf;                  // [chains] two scratch buffers
+    const SampleDesc* samples;      // [S]
+    const ChainDesc* chains;        // [chains]
+    const int4* reps;               // [R] (sample, chain, b, copy*NT + b)
+    const int2* tiles;              // [T] (replica, first h)
+    const long long* chain_off;     // [chains] element offset of buffer 0
+    unsigned long long* d_step;     // Philox step counter
+    unsigned long long seed;
+    double* part;                   // [T] per-tile energy partials
+    double* part9;                  // [2 T][9] per-tile overlap partials
+    double* Q;                      // [sum NT][9]
+    double* chi;                    // [sum NT]
+    int n_samples, n_chains, n_reps, n_tiles;
+    int max_NT;
+};
+
+// Half sweeps (kind 0 = overrelaxation, 1 = heat bath); `energy` also writes
+// the per-tile energy partials of the updated colour (valid for colour 1).
+cudaError_t launch_halfsweep(const DevBatch& b, bool fp64, int kind, bool energy, int color,
+                             int step_k, cudaStream_t st);
+cudaError_t launch_energy(const DevBatch& b, bool fp64, cudaStream_t st);
+cudaError_t launch_energy_finalize(const DevBatch& b, cudaStream_t st);
+cudaError_t launch_init_spins(const DevBatch& b, bool fp64, int ordered, cudaStream_t st);
+cudaError_t launch_advance_step(const DevBatch& b, int by, cudaStream_t st);
+cudaError_t launch_overlap(const DevBatch& b, bool fp64, cudaStream_t st);
+cudaError_t launch_exchange(const DevBatch& b, bool fp64, int mode, cudaStream_t st);
+
+}  // namespace ptk

@@ -1,0 +1,337 @@
+// pt_device.cuh -- device building blocks of the engine: counter-based random
+// numbers, checkerboard geometry, and the single-site moves of Hasenbusch &
+// Schaefer (arXiv:1006.4247) in float and double.
+#pragma once
+#include <cuda_runtime.h>
+#include <math_constants.h>
+#include <stdint.h>
+
+#include "pt_types.h"
+
+namespace ptk {
+
+// ---------------------------------------------------------------------------
+// Fast division (see FastDiv).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& f) {
+    return f.m == 0u ? n : (__umulhi(n, f.m) >> f.s);
+}
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32
+// multiplications with a Weyl-sequence key schedule.  Counter layout:
+// (c0, c1, step_lo, purpose << 24 | step_hi); key (seed_lo, seed_hi ^ sample).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint4 rng_words(uint64_t seed, uint32_t sample, uint32_t c0,
+                                           uint32_t c1, uint64_t step, uint32_t purpose) {
+    const uint2 k = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32) ^ sample);
+    const uint4 c = make_uint4(c0, c1, (uint32_t)step,
+                               (purpose << 24) | ((uint32_t)(step >> 32) & 0xFFFFFFu));
+    return philox4x32_10(c, k);
+}
+
+// u in [0,1) with 53 bits from two words.
+__device__ __forceinline__ double u53(uint32_t w0, uint32_t w1) {
+    return ((double)(w0 >> 5) * 67108864.0 + (double)(w1 >> 6)) * 0x1p-53;
+}
+
+// ---------------------------------------------------------------------------
+// Checkerboard geometry of one sample.
+// ---------------------------------------------------------------------------
+struct Site {
+    int h;              // index within the colour
+    int ih, j, k, i;    // coordinates
+    int x;              // natural site index i + L (j + L k)
+    int xp, xm;         // h of the +x / -x neighbours (other colour)
+    int yp, ym, zp, zm; // h of the +-y, +-z neighbours (other colour)
+};
+
+__device__ __forceinline__ Site site_of(const SampleDesc& sd, int color, int h) {
+    Site st;
+    st.h = h;
+    const uint32_t row = fdiv((uint32_t)h, sd.div_hL);
+    st.ih = h - (int)row * sd.hL;
+    const uint32_t kk = fdiv(row, sd.div_L);
+    st.k = (int)kk;
+    st.j = (int)row - st.k * sd.L;
+    const int p = (st.j + st.k + color) & 1;
+    st.i = 2 * st.ih + p;
+    st.x = st.i + sd.L * ((int)row);
+    const int hL = sd.hL, L = sd.L;
+    const int rowbase = (int)row * hL;
+    // x neighbours: same row of the other colour
+    int ixp = p ? st.ih + 1 : st.ih;
+    if (ixp == hL) ixp = 0;
+    int ixm = p ? st.ih : st.ih - 1;
+    if (ixm < 0) ixm = hL - 1;
+    st.xp = rowbase + ixp;
+    st.xm = rowbase + ixm;
+    const int jp = (st.j + 1 == L) ? 0 : st.j + 1;
+    const int jm = (st.j == 0) ? L - 1 : st.j - 1;
+    const int kp = (st.k + 1 == L) ? 0 : st.k + 1;
+    const int km = (st.k == 0) ? L - 1 : st.k - 1;
+    st.yp = st.ih + hL * (jp + L * st.k);
+    st.ym = st.ih + hL * (jm + L * st.k);
+    st.zp = st.ih + hL * (st.j + L * kp);
+    st.zm = st.ih + hL * (st.j + L * km);
+    return st;
+}
+
+// ---------------------------------------------------------------------------
+// Precision-dependent math.
+// ---------------------------------------------------------------------------
+template <typename T> struct M;
+template <> struct M<float> {
+    static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+    static __device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
+    static __device__ __forceinline__ float log_(float x) { return logf(x); }
+    static __device__ __forceinline__ float log1p_(float x) { return log1pf(x); }
+    static __device__ __forceinline__ float exp_(float x) { return expf(x); }
+    static __device__ __forceinline__ float expm1_(float x) { return expm1f(x); }
+    static __device__ __forceinline__ void sincos_(float x, float* s, float* c) { sincosf(x, s, c); }
+    static __device__ __forceinline__ float sin_(float x) { return sinf(x); }
+    static __device__ __forceinline__ float cos_(float x) { return cosf(x); }
+    static __device__ __forceinline__ float atan2_(float y, float x) { return atan2f(y, x); }
+    static __device__ __forceinline__ float copysign_(float a, float b) { return copysignf(a, b); }
+    static constexpr float tinyR = 1e-30f;
+    static constexpr int newton_iters = 6;
+    static constexpr float pi = CUDART_PI_F;
+};
+template <> struct M<double> {
+    static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+    static __device__ __forceinline__ double rsqrt_(double x) { return 1.0 / sqrt(x); }
+    static __device__ __forceinline__ double log_(double x) { return log(x); }
+    static __device__ __forceinline__ double log1p_(double x) { return log1p(x); }
+    static __device__ __forceinline__ double exp_(double x) { return exp(x); }
+    static __device__ __forceinline__ double expm1_(double x) { return expm1(x); }
+    static __device__ __forceinline__ void sincos_(double x, double* s, double* c) { sincos(x, s, c); }
+    static __device__ __forceinline__ double sin_(double x) { return sin(x); }
+    static __device__ __forceinline__ double cos_(double x) { return cos(x); }
+    static __device__ __forceinline__ double atan2_(double y, double x) { return atan2(y, x); }
+    static __device__ __forceinline__ double copysign_(double a, double b) { return copysign(a, b); }
+    static constexpr double tinyR = 1e-280;
+    static constexpr int newton_iters = 8;
+    static constexpr double pi = CUDART_PI;
+};
+
+template <typename T> struct V3 { T x, y, z; };
+
+template <typename T>
+__device__ __forceinline__ T dot(const V3<T>& a, const V3<T>& b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+
+template <typename T>
+__device__ __forceinline__ void renorm(V3<T>& s) {
+    T inv = M<T>::rsqrt_(dot(s, s));
+    s.x *= inv; s.y *= inv; s.z *= inv;
+}
+
+// Spin of colour array `arr` (base of [comp][half]) at h.
+template <typename T>
+__device__ __forceinline__ V3<T> ld3(const T* __restrict__ arr, int half, int h) {
+    V3<T> v;
+    v.x = arr[h];
+    v.y = arr[half + h];
+    v.z = arr[2 * half + h];
+    return v;
+}
+template <typename T>
+__device__ __forceinline__ void st3(T* __restrict__ arr, int half, int h, const V3<T>& v) {
+    arr[h] = v.x;
+    arr[half + h] = v.y;
+    arr[2 * half + h] = v.z;
+}
+
+// Neighbour field S_x = sum_y J_xy s_y (Eq. bigS).  `other` is the other
+// colour's [comp][half] array, Jown / Joth the colour-split forward couplings
+// ([mu][half]) of the site's colour and of the other colour.
+template <typename T>
+__device__ __forceinline__ V3<T> local_field(const Site& st, int half, const T* __restrict__ other,
+                                             const float* __restrict__ Jown,
+                                             const float* __restrict__ Joth) {
+    const T jxp = (T)__ldg(Jown + st.h), jyp = (T)__ldg(Jown + half + st.h),
+            jzp = (T)__ldg(Jown + 2 * half + st.h);
+    const T jxm = (T)__ldg(Joth + st.xm), jym = (T)__ldg(Joth + half + st.ym),
+            jzm = (T)__ldg(Joth + 2 * half + st.zm);
+    V3<T> S;
+    S.x = jxp * other[st.xp] + jxm * other[st.xm] + jyp * other[st.yp] + jym * other[st.ym] +
+          jzp * other[st.zp] + jzm * other[st.zm];
+    const T* oy = other + half;
+    S.y = jxp * oy[st.xp] + jxm * oy[st.xm] + jyp * oy[st.yp] + jym * oy[st.ym] +
+          jzp * oy[st.zp] + jzm * oy[st.zm];
+    const T* oz = other + 2 * half;
+    S.z = jxp * oz[st.xp] + jxm * oz[st.xm] + jyp * oz[st.yp] + jym * oz[st.ym] +
+          jzp * oz[st.zp] + jzm * oz[st.zm];
+    return S;
+}
+
+// ---------------------------------------------------------------------------
+// Heat bath (section III.C): cos(theta) along n = S/|S| from the inverse of
+// its conditional distribution, t = 1 - cos(theta) =
+// -ln(1 - q (1 - e^{-2R})) / R with R = beta |S| and q = 1 - r; the logarithm's
+// argument equals r + q e^{-2R}.  Azimuth phi in the basis of Duff et al.
+// (JCGT 2017) around n.  r and phi come from the two words w0, w1.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ V3<T> hb_site(T beta, const V3<T>& S, uint32_t w0, uint32_t w1) {
+    const T nS2 = dot(S, S);
+    const T nS = M<T>::sqrt_(nS2);
+    V3<T> n;
+    if (nS > (T)0) {
+        const T inv = (T)1 / nS;
+        n.x = S.x * inv; n.y = S.y * inv; n.z = S.z * inv;
+    } else {
+        n.x = (T)0; n.y = (T)0; n.z = (T)1;
+    }
+    const T R = beta * nS;
+    const T q = (T)(0xFFFFFFu - (w0 >> 8)) * (T)0x1p-24;
+    T t;
+    if (R < M<T>::tinyR) {
+        t = (T)2 * q;
+    } else {
+        const T a = -M<T>::expm1_((T)-2 * R);
+        const T qa = q * a;
+        if (qa <= (T)0.5)
+            t = -M<T>::log1p_(-qa) / R;
+        else
+            t = -M<T>::log_(((T)1 - q) + q * M<T>::exp_((T)-2 * R)) / R;
+    }
+    t = t < (T)0 ? (T)0 : (t > (T)2 ? (T)2 : t);
+    const T c = (T)1 - t;
+    const T st = M<T>::sqrt_(t * ((T)2 - t));
+    const T phi = (T)2 * M<T>::pi * ((T)(w1 >> 8) * (T)0x1p-24);
+    T sp, cp;
+    M<T>::sincos_(phi, &sp, &cp);
+    const T sgn = M<T>::copysign_((T)1, n.z);
+    const T a = (T)-1 / (sgn + n.z);
+    const T b = n.x * n.y * a;
+    const V3<T> e1 = {(T)1 + sgn * n.x * n.x * a, sgn * b, -sgn * n.x};
+    const V3<T> e2 = {b, sgn + n.y * n.y * a, -n.y};
+    V3<T> s;
+    s.x = c * n.x + st * (sp * e1.x + cp * e2.x);
+    s.y = c * n.y + st * (sp * e1.y + cp * e2.y);
+    s.z = c * n.z + st * (sp * e1.z + cp * e2.z);
+    renorm(s);
+    return s;
+}
+
+// Overrelaxation (section III.C): reflection of s about S; S = 0 keeps s.
+template <typename T>
+__device__ __forceinline__ void or_site(const V3<T>& S, V3<T>& s) {
+    const T SS = dot(S, S);
+    if (SS > (T)0) {
+        const T f = (T)2 * dot(s, S) / SS;
+        s.x = f * S.x - s.x;
+        s.y = f * S.y - s.y;
+        s.z = f * S.z - s.z;
+        renorm(s);
+    }
+}
+
+// ln(sinh R / R) = ln of I(beta S) / (4 pi) (Eq. HI); ln[2 sinh R] = R +
+// ln[1 - e^{-2R}] (appendix A).
+template <typename T>
+__device__ __forceinline__ T ln_sinhc(T R) {
+    if (R == (T)0) return (T)0;
+    if (R < (T)0.5) {
+        // ln(sinh R / R) = ln(-expm1(-2R) / (2R)) + R, accurate for small R
+        return M<T>::log_(-M<T>::expm1_((T)-2 * R) / ((T)2 * R)) + R;
+    }
+    return R + M<T>::log1p_(-M<T>::exp_((T)-2 * R)) - M<T>::log_((T)2 * R);
+}
+
+template <typename T>
+__device__ __forceinline__ T sinc_(T a) { return a == (T)0 ? (T)1 : M<T>::sin_(a) / a; }
+
+// Cooling step (section III.B): rotate s towards S by alpha = eps |p|,
+// p = S - (S.s) s; returns ln det J_f = ln[(1 - eps S.s)(cos a - eps S.s sinc a)].
+template <typename T>
+__device__ __forceinline__ T cool_site(T eps, const V3<T>& S, V3<T>& s) {
+    const T sS = dot(s, S);
+    const V3<T> p = {S.x - sS * s.x, S.y - sS * s.y, S.z - sS * s.z};
+    const T pn = M<T>::sqrt_(dot(p, p));
+    const T alpha = eps * pn;
+    const T ca = M<T>::cos_(alpha), sc = sinc_(alpha);
+    const T j = ((T)1 - eps * sS) * (ca - eps * sS * sc);
+    const T f = eps * sc;
+    s.x = s.x * ca + p.x * f;
+    s.y = s.y * ca + p.y * f;
+    s.z = s.z * ca + p.z * f;
+    renorm(s);
+    return M<T>::log_(fabs(j));
+}
+
+// Heating step = inverse cooling step: theta' given, solve
+// theta - e sin(theta) = theta' (e = eps |S| < 1) by a fixed number of Newton
+// iterations from theta' + e sin(theta'), rotate s' away from S by
+// theta - theta'.  Returns ln det J_f at the pre-image.
+template <typename T>
+__device__ __forceinline__ T heat_site(T eps, const V3<T>& S, V3<T>& s) {
+    const T nS = M<T>::sqrt_(dot(S, S));
+    const T sS = dot(s, S);
+    const V3<T> p = {S.x - sS * s.x, S.y - sS * s.y, S.z - sS * s.z};
+    const T pn = M<T>::sqrt_(dot(p, p));
+    const T e = eps * nS;
+    const T thp = M<T>::atan2_(pn, sS);
+    T th = thp + e * M<T>::sin_(thp);
+#pragma unroll
+    for (int it = 0; it < M<T>::newton_iters; ++it) {
+        T sn, cs;
+        M<T>::sincos_(th, &sn, &cs);
+        th -= (th - e * sn - thp) / ((T)1 - e * cs);
+        th = th < (T)0 ? (T)0 : (th > M<T>::pi ? M<T>::pi : th);
+    }
+    const T alpha = th - thp;
+    if (pn > (T)0) {
+        T sa, ca;
+        M<T>::sincos_(alpha, &sa, &ca);
+        const T f = sa / pn;
+        s.x = s.x * ca - p.x * f;
+        s.y = s.y * ca - p.y * f;
+        s.z = s.z * ca - p.z * f;
+        renorm(s);
+    }
+    T sth, cth;
+    M<T>::sincos_(th, &sth, &cth);
+    const T al = e * sth;
+    const T j = ((T)1 - e * cth) * (M<T>::cos_(al) - e * cth * sinc_(al));
+    return M<T>::log_(fabs(j));
+}
+
+// ---------------------------------------------------------------------------
+// Deterministic block reduction of a double (blockDim.x multiple of 32,
+// <= 1024).  All threads must call it; the result is valid in thread 0.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double block_sum(double v, double* sh /* >= 32 doubles */) {
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    double r = 0.0;
+    if (wid == 0) {
+        r = (lane < nw) ? sh[lane] : 0.0;
+        r = warp_sum(r);
+    }
+    return r;
+}
+
+}  // namespace ptk

@@ -1,0 +1,385 @@
+"""Python binding of the C ABI in include/pt.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of the method: all of the sweep, exchange and measurement work runs
+in the CUDA kernels of libpt.so.  If the library has not been built the first
+call raises; there is no fallback.
+
+PyTorch, when present, supplies the CUDA stream (``torch.cuda.current_stream``)
+and may own the device memory through the allocator callback
+(``use_torch_allocator=True``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libpt.so")
+
+PT_OK, PT_ERR_ARG, PT_ERR_ODD_L, PT_ERR_EPS, PT_ERR_CUDA, PT_ERR_TIMEOUT, PT_ERR_STATE, PT_ERR_NOMEM = (
+    0, -1, -2, -3, -4, -5, -6, -7)
+PT_PLAIN, PT_DECIMATION, PT_COOLHEAT = 0, 1, 2
+PT_FP32, PT_FP64 = 0, 1
+PT_START_RANDOM, PT_START_ORDERED = 0, 1
+MODES = {"plain": PT_PLAIN, "decimation": PT_DECIMATION, "coolheat": PT_COOLHEAT}
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+# Entry points declared in include/pt.h (the symbol test checks this list
+# against the header).
+ENTRY_POINTS = ["pt_options_default", "pt_create", "pt_create_batch", "pt_sweep", "pt_exchange",
+                "pt_measure", "pt_measure_device", "pt_get_stats", "pt_get_spins", "pt_set_spins",
+                "pt_set_params", "pt_set_rng_step", "pt_get_rng_step", "pt_save", "pt_load",
+                "pt_profile", "pt_profile_read", "pt_destroy", "pt_last_error"]
+PT_KERNEL_KINDS = 6
+KERNEL_KINDS = ["hb", "or", "energy", "exchange", "measure", "other"]
+
+
+class PtOptions(C.Structure):
+    _fields_ = [("n_samples", C.c_int), ("n_copies", C.c_int), ("precision", C.c_int),
+                ("seed", C.c_uint64), ("start", C.c_int), ("stream", C.c_void_p),
+                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p)]
+
+
+class PtError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"pt status {status}: {msg}")
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libpt.so; raise if it was not built (no fallback exists)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise ImportError(f"{path} not found: build the engine first "
+                                  "(python -c 'import __graft_entry__ as g; g.build()')")
+            lib = C.CDLL(path)
+            vp, ip, dp, fp = C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_float)
+            i64p, i32p = C.POINTER(C.c_int64), C.POINTER(C.c_int32)
+            sig = {
+                "pt_options_default": (None, [C.POINTER(PtOptions)]),
+                "pt_create": (ip, [C.POINTER(vp), ip, fp, dp, ip, C.POINTER(PtOptions)]),
+                "pt_create_batch": (ip, [C.POINTER(vp), ip, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                         C.POINTER(fp), C.POINTER(dp), C.POINTER(PtOptions)]),
+                "pt_sweep": (ip, [vp, ip, ip]),
+                "pt_exchange": (ip, [vp, ip, fp]),
+                "pt_measure": (ip, [vp, dp, dp, dp]),
+                "pt_measure_device": (ip, [vp, vp, vp, vp]),
+                "pt_profile": (ip, [vp, ip]),
+                "pt_profile_read": (ip, [vp, dp, i64p]),
+                "pt_get_stats": (ip, [vp, i64p, i64p, i64p, i32p]),
+                "pt_get_spins": (ip, [vp, ip, ip, ip, dp]),
+                "pt_set_spins": (ip, [vp, ip, ip, ip, dp]),
+                "pt_set_params": (ip, [vp, dp, fp]),
+                "pt_set_rng_step": (ip, [vp, C.c_uint64]),
+                "pt_get_rng_step": (ip, [vp, C.POINTER(C.c_uint64)]),
+                "pt_save": (ip, [vp, C.c_char_p]),
+                "pt_load": (ip, [vp, C.c_char_p]),
+                "pt_destroy": (ip, [vp]),
+                "pt_last_error": (C.c_char_p, []),
+            }
+            for name, (res, args) in sig.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _check(st):
+    if st != PT_OK:
+        raise PtError(st, load_library().pt_last_error().decode(errors="replace"))
+
+
+def _ptr(a, ctype):
+    return None if a is None else a.ctypes.data_as(C.POINTER(ctype))
+
+
+def pt_last_error() -> str:
+    return load_library().pt_last_error().decode(errors="replace")
+
+
+def pt_options_default() -> PtOptions:
+    o = PtOptions()
+    load_library().pt_options_default(C.byref(o))
+    return o
+
+
+def pt_create(L, couplings, betas, n_replicas, opt: PtOptions | None = None):
+    """couplings float32 [S, 3, L^3]; betas float64 [S, n_replicas]."""
+    J = np.ascontiguousarray(couplings, np.float32)
+    B = np.ascontiguousarray(betas, np.float64)
+    h = C.c_void_p()
+    _check(load_library().pt_create(C.byref(h), int(L), _ptr(J, C.c_float), _ptr(B, C.c_double),
+                                    int(n_replicas), None if opt is None else C.byref(opt)))
+    return h
+
+
+def pt_create_batch(L, n_replicas, couplings, betas, opt: PtOptions | None = None):
+    """Per-sample lists: L[s], n_replicas[s], couplings[s] float32 [3, L^3],
+    betas[s] float64 [n_replicas[s]]."""
+    S = len(L)
+    Ls = (C.c_int * S)(*[int(v) for v in L])
+    NTs = (C.c_int * S)(*[int(v) for v in n_replicas])
+    Js = [np.ascontiguousarray(j, np.float32) for j in couplings]
+    Bs = [np.ascontiguousarray(b, np.float64) for b in betas]
+    Jp = (C.POINTER(C.c_float) * S)(*[_ptr(j, C.c_float) for j in Js])
+    Bp = (C.POINTER(C.c_double) * S)(*[_ptr(b, C.c_double) for b in Bs])
+    h = C.c_void_p()
+    _check(load_library().pt_create_batch(C.byref(h), S, Ls, NTs, Jp, Bp,
+                                          None if opt is None else C.byref(opt)))
+    return h
+
+
+def pt_sweep(h, n_hb, n_or):
+    _check(load_library().pt_sweep(h, int(n_hb), int(n_or)))
+
+
+def pt_exchange(h, mode, eps=None):
+    mode = MODES.get(mode, mode) if isinstance(mode, str) else int(mode)
+    e = None if eps is None else np.ascontiguousarray(eps, np.float32)
+    _check(load_library().pt_exchange(h, mode, _ptr(e, C.c_float)))
+
+
+def pt_measure(h, energy=None, overlap=None, chi=None):
+    """Fill the given float64 arrays (any may be None)."""
+    _check(load_library().pt_measure(h, _ptr(energy, C.c_double), _ptr(overlap, C.c_double),
+                                     _ptr(chi, C.c_double)))
+
+
+def pt_measure_device(h, d_energy=None, d_overlap=None, d_chi=None):
+    """Enqueue the reductions into device buffers (integer device pointers or
+    None) without synchronising."""
+    _check(load_library().pt_measure_device(h, d_energy, d_overlap, d_chi))
+
+
+def pt_profile(h, enable):
+    _check(load_library().pt_profile(h, int(enable)))
+
+
+def pt_profile_read(h):
+    """Return ({kind: ms}, {kind: launches}) since the last pt_profile call."""
+    ms = np.zeros(PT_KERNEL_KINDS)
+    n = np.zeros(PT_KERNEL_KINDS, np.int64)
+    _check(load_library().pt_profile_read(h, _ptr(ms, C.c_double), _ptr(n, C.c_int64)))
+    return dict(zip(KERNEL_KINDS, ms.tolist())), dict(zip(KERNEL_KINDS, n.tolist()))
+
+
+def pt_get_stats(h, proposals=None, accepts=None, round_trips=None, perm=None):
+    _check(load_library().pt_get_stats(h, _ptr(proposals, C.c_int64), _ptr(accepts, C.c_int64),
+                                       _ptr(round_trips, C.c_int64), _ptr(perm, C.c_int32)))
+
+
+def pt_get_spins(h, sample, copy, replica, out):
+    _check(load_library().pt_get_spins(h, int(sample), int(copy), int(replica), _ptr(out, C.c_double)))
+
+
+def pt_set_spins(h, sample, copy, replica, xyz):
+    a = np.ascontiguousarray(xyz, np.float64)
+    _check(load_library().pt_set_spins(h, int(sample), int(copy), int(replica), _ptr(a, C.c_double)))
+
+
+def pt_set_params(h, betas=None, eps=None):
+    b = None if betas is None else np.ascontiguousarray(betas, np.float64)
+    e = None if eps is None else np.ascontiguousarray(eps, np.float32)
+    _check(load_library().pt_set_params(h, _ptr(b, C.c_double), _ptr(e, C.c_float)))
+
+
+def pt_set_rng_step(h, step):
+    _check(load_library().pt_set_rng_step(h, int(step)))
+
+
+def pt_get_rng_step(h) -> int:
+    v = C.c_uint64()
+    _check(load_library().pt_get_rng_step(h, C.byref(v)))
+    return int(v.value)
+
+
+def pt_save(h, path):
+    _check(load_library().pt_save(h, os.fsencode(path)))
+
+
+def pt_load(h, path):
+    _check(load_library().pt_load(h, os.fsencode(path)))
+
+
+def pt_destroy(h):
+    _check(load_library().pt_destroy(h))
+
+
+# --------------------------------------------------------------------------
+# Convenience wrapper: shapes, numpy outputs, torch stream / allocator.
+# --------------------------------------------------------------------------
+def _torch_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return None
+
+
+class _TorchAllocator:
+    """Device memory from PyTorch's caching allocator."""
+
+    def __init__(self):
+        import torch
+        self.torch = torch
+        self.dev = torch.cuda.current_device()
+
+        def _alloc(n, ctx):
+            return int(torch.cuda.caching_allocator_alloc(int(n), self.dev))
+
+        def _free(p, ctx):
+            torch.cuda.caching_allocator_delete(int(p))
+
+        self.alloc = ALLOC_FN(_alloc)
+        self.free = FREE_FN(_free)
+
+
+class Engine:
+    """A batch of disorder samples with shapes kept on the Python side."""
+
+    def __init__(self, L, couplings, betas, n_copies=2, precision="fp32", seed=0,
+                 start="random", stream=None, use_torch_allocator=False):
+        uneven = isinstance(L, (list, tuple))
+        opt = pt_options_default()
+        opt.n_copies = n_copies
+        opt.precision = PT_FP64 if precision in ("fp64", PT_FP64) else PT_FP32
+        opt.seed = seed & 0xFFFFFFFFFFFFFFFF
+        opt.start = PT_START_ORDERED if start in ("ordered", PT_START_ORDERED) else PT_START_RANDOM
+        st = _torch_stream() if stream is None else stream
+        opt.stream = st
+        self._alloc = None
+        if use_torch_allocator:
+            self._alloc = _TorchAllocator()
+            opt.alloc = self._alloc.alloc
+            opt.free = self._alloc.free
+        self.C = n_copies
+        if uneven:
+            self.L = [int(v) for v in L]
+            self.NT = [len(b) for b in betas]
+            opt.n_samples = len(self.L)
+            self.h = pt_create_batch(self.L, self.NT, couplings, betas, opt)
+        else:
+            J = np.asarray(couplings, np.float32)
+            if J.ndim == 2:
+                J = J[None]
+            B = np.asarray(betas, np.float64)
+            if B.ndim == 1:
+                B = np.broadcast_to(B, (J.shape[0], B.size))
+            opt.n_samples = J.shape[0]
+            self.L = [int(L)] * J.shape[0]
+            self.NT = [B.shape[1]] * J.shape[0]
+            self.h = pt_create(L, J, B, B.shape[1], opt)
+        self.S = len(self.L)
+        self.uniform = not uneven
+        self.R = sum(self.C * n for n in self.NT)
+        self.P = sum(self.C * (n - 1) for n in self.NT)
+
+    # shapes -------------------------------------------------------------
+    def _shape(self, per_sample, rect):
+        return rect if self.uniform else (per_sample,)
+
+    def sweep(self, n_hb=1, n_or=1):
+        pt_sweep(self.h, n_hb, n_or)
+
+    def exchange(self, mode="plain", eps=None):
+        pt_exchange(self.h, mode, eps)
+
+    def energies(self):
+        out = np.zeros(self.R)
+        pt_measure(self.h, energy=out)
+        return out.reshape(self.S, self.C, self.NT[0]) if self.uniform else out
+
+    def overlap(self):
+        n = sum(self.NT)
+        Q = np.zeros(n * 9)
+        chi = np.zeros(n)
+        pt_measure(self.h, overlap=Q, chi=chi)
+        if self.uniform:
+            return Q.reshape(self.S, self.NT[0], 3, 3), chi.reshape(self.S, self.NT[0])
+        return Q.reshape(n, 3, 3), chi
+
+    def measure(self):
+        n = sum(self.NT)
+        H = np.zeros(self.R)
+        Q = np.zeros(n * 9) if self.C == 2 else None
+        chi = np.zeros(n) if self.C == 2 else None
+        pt_measure(self.h, H, Q, chi)
+        return H, Q, chi
+
+    def measure_device(self):
+        pt_measure_device(self.h)
+
+    def profile(self, enable=True):
+        pt_profile(self.h, enable)
+
+    def profile_read(self):
+        return pt_profile_read(self.h)
+
+    def stats(self):
+        prop = np.zeros(self.P, np.int64)
+        acc = np.zeros(self.P, np.int64)
+        rt = np.zeros(self.S * self.C, np.int64)
+        perm = np.zeros(self.R, np.int32)
+        pt_get_stats(self.h, prop, acc, rt, perm)
+        if self.uniform:
+            NT = self.NT[0]
+            return (prop.reshape(self.S, self.C, NT - 1), acc.reshape(self.S, self.C, NT - 1),
+                    rt.reshape(self.S, self.C), perm.reshape(self.S, self.C, NT))
+        return prop, acc, rt, perm
+
+    def get_spins(self, sample, copy, replica):
+        out = np.zeros((self.L[sample] ** 3, 3))
+        pt_get_spins(self.h, sample, copy, replica, out)
+        return out
+
+    def set_spins(self, sample, copy, replica, xyz):
+        pt_set_spins(self.h, sample, copy, replica, xyz)
+
+    def set_params(self, betas=None, eps=None):
+        pt_set_params(self.h, betas, eps)
+
+    @property
+    def step(self):
+        return pt_get_rng_step(self.h)
+
+    @step.setter
+    def step(self, v):
+        pt_set_rng_step(self.h, v)
+
+    def save(self, path):
+        pt_save(self.h, path)
+
+    def load(self, path):
+        pt_load(self.h, path)
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            pt_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,250 @@
+"""GPU parity of every kernel of the hot path against the FP64 oracle, element
+by element, on seeded inputs: initial spins, heat-bath and overrelaxation half
+sweeps, energies, overlap, and the three exchanges.  Lattice sizes cover a
+single partial tile (L = 4, 6), several tiles with a ragged tail (L = 12) and
+full tiles (L = 16); uneven batches mix sizes in one launch.
+
+Tolerances: double precision 1e-12 per spin component (spec bound);
+single precision 1e-5 per spin component after one sweep, relative 1e-5 on
+energies; integer bookkeeping bit-exact."""
+import numpy as np
+import pytest
+
+import oracle as orc
+from gpu_util import ambiguous_basis_sites, get_state, make_engine, set_random_state, site_colour
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32": 1e-5}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1006_4247_gb300 import _build
+    _build.build()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("L", [2, 4, 6, 12])
+def test_initial_spins(precision, L):
+    S, C, NT = 2, 2, 3
+    eng, J, B = make_engine(L, S, NT, C, precision, seed=77)
+    st = get_state(eng, S, C, NT)
+    for s in range(S):
+        for c in range(C):
+            for b in range(NT):
+                ref = orc.init_spins(L, 0, 77, s, c * NT + b)
+                assert np.abs(st[s, c, b] - ref).max() <= TOL[precision], (s, c, b)
+    eng.close()
+    eng, J, B = make_engine(L, S, NT, C, precision, start="ordered")
+    assert (get_state(eng, S, C, NT) == np.array([1.0, 0.0, 0.0])).all()
+    eng.close()
+
+
+@pytest.mark.parametrize("L", [2, 4, 6, 12, 16])
+def test_energy_and_overlap(L):
+    S, C, NT = 2, 2, 3
+    for precision in ("fp64", "fp32"):
+        eng, J, B = make_engine(L, S, NT, C, precision)
+        st = set_random_state(eng, S, C, NT, L, seed=5)
+        H = eng.energies()
+        Q, chi = eng.overlap()
+        for s in range(S):
+            for c in range(C):
+                for b in range(NT):
+                    ref = orc.energy(L, J[s], st[s, c, b])
+                    tol = 1e-11 if precision == "fp64" else 2e-5
+                    assert abs(H[s, c, b] - ref) <= tol * max(1.0, abs(ref))
+            for b in range(NT):
+                Qr, chir = orc.overlap(L, st[s, 0, b], st[s, 1, b])
+                tol = 1e-10 if precision == "fp64" else 1e-4
+                assert np.abs(Q[s, b] - Qr).max() <= tol * max(1.0, np.abs(Qr).max())
+                assert abs(chi[s, b] - chir) <= tol * max(1.0, chir)
+        eng.close()
+
+
+def _oracle_sweep(L, J, s, beta, kind, seed, sample, rep_id, step):
+    t = s.copy()
+    for colour in (0, 1):
+        if kind == "hb":
+            t = orc.hb_halfsweep(L, J, t, colour, beta, seed, sample, rep_id, step + colour)
+        else:
+            t = orc.or_halfsweep(L, J, t, colour)
+    return t
+
+
+@pytest.mark.parametrize("L", [2, 4, 6, 12, 16])
+@pytest.mark.parametrize("kind", ["hb", "or"])
+def test_one_sweep_fp64(L, kind):
+    """One sweep (colour 0 then colour 1) from an identical state with identical
+    Philox counters matches the oracle to 1e-12."""
+    S, C, NT, seed = 2, 2, 3, 21
+    eng, J, B = make_engine(L, S, NT, C, "fp64", seed=seed)
+    st = set_random_state(eng, S, C, NT, L, seed=9)
+    step0 = 1234567
+    eng.step = step0
+    eng.sweep(1, 0) if kind == "hb" else eng.sweep(0, 1)
+    out = get_state(eng, S, C, NT)
+    assert eng.step == step0 + 2
+    for s in range(S):
+        for c in range(C):
+            for b in range(NT):
+                ref = _oracle_sweep(L, J[s], st[s, c, b], B[s, b], kind, seed, s, c * NT + b, step0)
+                assert np.abs(out[s, c, b] - ref).max() <= 1e-12, (s, c, b)
+    # the fused energy of the last half sweep equals the oracle's H
+    H = eng.energies()
+    for s in range(S):
+        for c in range(C):
+            for b in range(NT):
+                ref = orc.energy(L, J[s], out[s, c, b])
+                assert abs(H[s, c, b] - ref) <= 1e-11 * max(1, abs(ref))
+    eng.close()
+
+
+@pytest.mark.parametrize("L", [4, 12, 16])
+@pytest.mark.parametrize("kind", ["hb", "or"])
+def test_one_sweep_fp32(L, kind):
+    """Single precision: each half sweep is checked site by site, the second
+    one from the engine's own first-half result (the oracle computes every
+    site from the same neighbours); where the heat-bath basis orientation is
+    ambiguous only the component along S and |s| = 1 are compared."""
+    S, C, NT, seed = 1, 2, 3, 23
+    eng, J, B = make_engine(L, S, NT, C, "fp32", seed=seed)
+    st = set_random_state(eng, S, C, NT, L, seed=19)
+    step0 = 99
+    eng.step = step0
+    eng.sweep(1, 0) if kind == "hb" else eng.sweep(0, 1)
+    out = get_state(eng, S, C, NT)
+    col = site_colour(L)
+    for c in range(C):
+        for b in range(NT):
+            cur = st[0, c, b].copy()
+            for colour in (0, 1):
+                if kind == "hb":
+                    ref = orc.hb_halfsweep(L, J[0], cur, colour, B[0, b], seed, 0, c * NT + b, step0 + colour)
+                    amb = ambiguous_basis_sites(L, J[0], cur, colour)
+                else:
+                    ref = orc.or_halfsweep(L, J[0], cur, colour)
+                    amb = np.zeros(L ** 3, bool)
+                m = (col == colour) & ~amb
+                assert np.abs(out[0, c, b][m] - ref[m]).max() <= 1e-5, (c, b, colour)
+                for x in np.nonzero((col == colour) & amb)[0]:
+                    Sx = orc.local_field(L, J[0], cur, x)
+                    n = Sx / np.linalg.norm(Sx)
+                    assert abs(out[0, c, b][x] @ n - ref[x] @ n) <= 1e-5
+                # continue from the engine's half-sweep result
+                cur = cur.copy()
+                cur[col == colour] = out[0, c, b][col == colour]
+            assert np.allclose(np.linalg.norm(out[0, c, b], axis=1), 1.0, atol=1e-6)
+    eng.close()
+
+
+def _oracle_chains(eng_state, J, B, S, C, NT, L, seed):
+    chains = []
+    for s in range(S):
+        for c in range(C):
+            chains.append(orc.Chain(L, J[s], B[s], eng_state[s, c], copy=c, sample=s, seed=seed))
+    return chains
+
+
+@pytest.mark.parametrize("mode", ["plain", "decimation", "coolheat"])
+@pytest.mark.parametrize("L", [4, 6, 12])
+def test_exchange_fp64(mode, L):
+    """One tempering update from identical state: permutation, counters,
+    round trips bit-exact; spins (re-inserted or transformed) to 1e-12;
+    energies to 1e-11."""
+    S, C, NT, seed = 2, 2, 6, 31
+    eng, J, B = make_engine(L, S, NT, C, "fp64", seed=seed, bmin=1.8, bmax=2.4)
+    st = set_random_state(eng, S, C, NT, L, seed=29)
+    chains = _oracle_chains(st, J, B, S, C, NT, L, seed)
+    eps = np.full((S, NT - 1), 0.02, np.float32)
+    for rnd in range(4):
+        step = eng.step
+        eng.exchange(mode, eps if mode == "coolheat" else None)
+        for ch in chains:
+            ch.exchange({"plain": 0, "decimation": 1, "coolheat": 2}[mode], step, eps=eps[0])
+        prop, acc, rt, perm = eng.stats()
+        H = eng.energies()
+        out = get_state(eng, S, C, NT)
+        for s in range(S):
+            for c in range(C):
+                ch = chains[s * C + c]
+                assert (perm[s, c] == ch.label).all(), (rnd, s, c)
+                assert (prop[s, c] == ch.prop).all() and (acc[s, c] == ch.acc).all()
+                assert rt[s, c] == ch.rt_count[0]
+                assert np.abs(out[s, c] - ch.spins).max() <= 1e-12
+                assert np.abs(H[s, c] - ch.H).max() <= 1e-11 * max(1.0, np.abs(ch.H).max())
+        # move the state on and start the next update from an identical state
+        # (the oracle takes the engine's spins; its bookkeeping continues)
+        eng.sweep(0, 1)
+        new = get_state(eng, S, C, NT)
+        for s in range(S):
+            for c in range(C):
+                ch = chains[s * C + c]
+                ch.spins[:] = new[s, c]
+                for b in range(NT):
+                    ch.H[b] = orc.energy(L, ch.J, ch.spins[b])
+    assert sum(int(c.acc.sum()) for c in chains) > 0
+    eng.close()
+
+
+@pytest.mark.parametrize("mode", ["plain", "decimation", "coolheat"])
+def test_exchange_fp32_statistics_match_decisions(mode):
+    """Single precision exchange from an identical state: decisions agree with
+    the oracle's except where |ln A| is within float round-off of ln u."""
+    L, S, C, NT, seed = 6, 4, 2, 6, 41
+    eng, J, B = make_engine(L, S, NT, C, "fp32", seed=seed, bmin=1.8, bmax=2.4)
+    st = set_random_state(eng, S, C, NT, L, seed=39)
+    chains = _oracle_chains(st, J, B, S, C, NT, L, seed)
+    eps = np.full((S, NT - 1), 0.02, np.float32)
+    step = eng.step
+    eng.exchange(mode, eps if mode == "coolheat" else None)
+    for ch in chains:
+        ch.exchange({"plain": 0, "decimation": 1, "coolheat": 2}[mode], step, eps=eps[0])
+    prop, acc, rt, perm = eng.stats()
+    agree = sum(int((perm[s, c] == chains[s * C + c].label).all()) for s in range(S) for c in range(C))
+    assert agree >= S * C - 1
+    eng.close()
+
+
+def test_uneven_batch_parity():
+    """Samples of different L and replica counts in one engine (one launch per
+    half sweep) match the oracle sample by sample."""
+    from paper_1006_4247_gb300 import pt
+    from paper_1006_4247_gb300 import workloads as W
+    Ls = [4, 6, 8, 2, 12]
+    NTs = [3, 5, 2, 4, 3]
+    Js = [W.couplings(L, 500 + i) for i, L in enumerate(Ls)]
+    Bs = [W.linear_betas(n, 0.7, 1.9) for n in NTs]
+    seed = 51
+    eng = pt.Engine(Ls, Js, Bs, n_copies=2, precision="fp64", seed=seed)
+    for s, L in enumerate(Ls):
+        for c in range(2):
+            for b in range(NTs[s]):
+                ref = orc.init_spins(L, 0, seed, s, c * NTs[s] + b)
+                assert np.abs(eng.get_spins(s, c, b) - ref).max() <= 1e-12
+    before = [[[eng.get_spins(s, c, b) for b in range(NTs[s])] for c in range(2)] for s in range(len(Ls))]
+    step0 = eng.step
+    eng.sweep(1, 1)
+    for s, L in enumerate(Ls):
+        J = Js[s].astype(np.float64)
+        for c in range(2):
+            for b in range(NTs[s]):
+                ref = _oracle_sweep(L, J, before[s][c][b], Bs[s][b], "hb", seed, s, c * NTs[s] + b, step0)
+                ref = _oracle_sweep(L, J, ref, Bs[s][b], "or", seed, s, 0, 0)
+                assert np.abs(eng.get_spins(s, c, b) - ref).max() <= 1e-12, (s, c, b)
+    H, Q, chi = eng.measure()
+    off = 0
+    qoff = 0
+    for s, L in enumerate(Ls):
+        J = Js[s].astype(np.float64)
+        for c in range(2):
+            for b in range(NTs[s]):
+                ref = orc.energy(L, J, eng.get_spins(s, c, b))
+                assert abs(H[off] - ref) <= 1e-11 * max(1, abs(ref))
+                off += 1
+        for b in range(NTs[s]):
+            Qr, chir = orc.overlap(L, eng.get_spins(s, 0, b), eng.get_spins(s, 1, b))
+            assert abs(chi[qoff] - chir) <= 1e-10 * max(1, chir)
+            qoff += 1
+    eng.close()
