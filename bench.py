@@ -47,6 +47,7 @@ def parse():
     p.add_argument("--exchange", default=None)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    p.add_argument("--policy", default="auto", choices=["auto", "streaming", "resident"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     return p.parse_args()
@@ -239,6 +240,7 @@ def ours(args):
                     stream=stream.cuda_stream)
     eps = eps_array(w)
     eng.set_params(eps=eps)
+    eng.set_policy(args.policy)
     mode = w.exchange
 
     def step():
@@ -246,29 +248,32 @@ def ours(args):
         eng.exchange(mode)
         eng.measure_device()
 
-    for _ in range(max(args.warmup, 3)):
-        step()
-    torch.cuda.synchronize()
-
     def barrier():
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
+    def timed(nsteps):
+        eng.profile(True)
+        barrier()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(nsteps):
+            step()
+        ev1.record(stream)
+        barrier()
+        t = ev0.elapsed_time(ev1)
+        pm, ln = eng.profile_read()
+        eng.profile(False)
+        return t, pm, ln
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
-    eng.profile(True)
-    barrier()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(args.steps):
-        step()
-    ev1.record(stream)
-    barrier()
-    ms = ev0.elapsed_time(ev1)
-    prof_ms, launches = eng.profile_read()
-    eng.profile(False)
+    ms, prof_ms, launches = timed(args.steps)
     clk = clocks.stop()
     if world > 1:
         t = torch.tensor([ms], device="cuda")
@@ -277,22 +282,47 @@ def ours(args):
     ups = updates_per_step(w)
     value = ups * args.steps * world / (ms * 1e6)
 
-    # roofline of the overrelaxation half sweep
     NT, L, S, C = w.n_replicas[0], w.L[0], w.n_samples, w.n_copies
     N = L ** 3
     R = S * C * NT
     bpe = 4 if args.precision == "fp32" else 8
-    alg_bytes = R * (N // 2) * 9 * bpe + S * 3 * N * 4
-    n_or_launch = launches["or"]
-    or_avg_s = prof_ms["or"] / max(n_or_launch, 1) / 1e3
-    achieved = alg_bytes / or_avg_s / 1e9
     peak, peak_src = load_peaks()
-    traffic = ncu_traffic(w.name, args.precision)
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": traffic, "kernel": "k_halfsweep<OR>",
-            "peak_source": peak_src, "alg_bytes_per_launch": alg_bytes,
-            "avg_launch_us": or_avg_s * 1e6}
+
+    def or_roofline(pm, ln):
+        """HBM roofline of the streaming overrelaxation half sweep: 36 B per
+        update in float (read own + write own + read the other colour), plus
+        the sample's couplings once per half sweep."""
+        alg = R * (N // 2) * 9 * bpe + S * 3 * N * 4
+        avg = pm["or"] / max(ln["or"], 1) / 1e3
+        ach = alg / avg / 1e9
+        return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "traffic": ncu_traffic(w.name, args.precision), "kernel": "k_sweep<OR> (streaming half sweep)",
+                "peak_source": peak_src, "alg_bytes_per_launch": alg, "avg_launch_us": avg * 1e6}
+
+    dominant = max(prof_ms, key=prof_ms.get)
     share = {k: v / max(sum(prof_ms.values()), 1e-9) for k, v in prof_ms.items()}
+    streaming = None
+    if dominant == "resident":
+        # the resident block reads and writes each replica once per cycle; its
+        # limit is the on-chip data path, reported against the FP32 issue rate
+        flops_per_update = 60.0
+        n_launch = max(launches["resident"], 1)
+        avg = prof_ms["resident"] / n_launch / 1e3
+        alg_flops = ups * flops_per_update
+        peak_alu = 152 * 128 * 2 * 2.07e9
+        roof = {"bound": "alu", "achieved": alg_flops / avg / 1e12, "peak": peak_alu / 1e12, "unit": "TFLOP/s",
+                "frac": alg_flops / avg / peak_alu, "traffic": None, "kernel": "k_resident (sweep block in shared memory)",
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz",
+                "alg_flops_per_launch": alg_flops, "avg_launch_us": avg * 1e6,
+                "effective_hbm_GBps": ups * 36.4 / avg / 1e9}
+        eng.set_policy("streaming")
+        for _ in range(2):
+            step()
+        _, pm2, ln2 = timed(max(2, args.steps // 2))
+        streaming = or_roofline(pm2, ln2)
+        eng.set_policy(args.policy)
+    else:
+        roof = or_roofline(prof_ms, launches)
 
     # end to end through the public API with host buffers
     e2e = None
@@ -342,9 +372,10 @@ def ours(args):
             "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
             "config": {"workload": w.name, "L": L, "samples": S, "replicas": NT, "copies": C,
                        "n_hb": w.n_hb, "n_or": w.n_or, "exchange": mode, "eps": w.eps,
-                       "precision": args.precision, "parallelism": f"samples sharded x{world}",
+                       "precision": args.precision, "policy": args.policy,
+                       "parallelism": f"samples sharded x{world}",
                        "l2": f"inputs larger than L2 ({spins_bytes / 1e6:.0f} MB of spins > 129 MB)"},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "streaming_roofline": streaming,
             "gpu_launches": int(sum(launches.values())), "clocks": clk,
             "kernel_share": share, "kernel_ms": prof_ms, "kernel_launches": launches,
         }

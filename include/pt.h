@@ -202,10 +202,22 @@ typedef enum {
     PT_KERNEL_EXCHANGE = 3,  /* tempering updates */
     PT_KERNEL_MEASURE = 4,   /* overlap reduction */
     PT_KERNEL_OTHER = 5,     /* initial spins, step counter */
-    PT_KERNEL_KINDS = 6
+    PT_KERNEL_RESIDENT = 6,  /* whole sweep blocks of a replica held in shared memory */
+    PT_KERNEL_KINDS = 7
 } pt_kernel_kind;
 pt_status pt_profile(pt_handle h, int enable);
 pt_status pt_profile_read(pt_handle h, double *ms, int64_t *launches);
+
+/* Choose how pt_sweep runs the local updates.
+ *   PT_POLICY_AUTO (default): shared-memory resident sweep blocks when every
+ *     sample's replica fits (float: L/2 divisible by 4 and at most 100 KB of
+ *     spins per replica, e.g. L = 8, 16; double: L/2 even, at most 100 KB),
+ *     else streaming half sweeps;
+ *   PT_POLICY_STREAMING: one kernel per half sweep over HBM;
+ *   PT_POLICY_RESIDENT: resident blocks; PT_ERR_STATE if a sample does not fit.
+ * Both give the same chain (same updates, same random numbers). */
+typedef enum { PT_POLICY_AUTO = 0, PT_POLICY_STREAMING = 1, PT_POLICY_RESIDENT = 2 } pt_policy;
+pt_status pt_set_policy(pt_handle h, int policy);
 
 /* Release all device memory of the handle.  NULL is accepted. */
 pt_status pt_destroy(pt_handle h);

@@ -464,19 +464,20 @@ double orc_cool_site(double eps, const double S[3], double s[3])
 
 /* Inverse of the cooling step: theta' given, solve
  * theta - e sin(theta) = theta', e = eps |S| < 1, by Newton's method
- * (section III.B), then rotate s' away from S by alpha = theta - theta'.
- * Returns ln det J_f evaluated at the pre-image. */
-int orc_newton_iters = 8;
-
+ * (section III.B) from theta' + e sin(theta') until the step is below
+ * 1e-15 (at most 50 steps), then rotate s' away from S by
+ * alpha = theta - theta'.  Returns ln det J_f evaluated at the pre-image. */
 double orc_kepler_solve(double e, double thp)
 {
     double th = thp + e * sin(thp);
-    for (int it = 0; it < orc_newton_iters; ++it) {
+    for (int it = 0; it < 50; ++it) {
         double f = th - e * sin(th) - thp;
         double fp = 1.0 - e * cos(th);
-        th -= f / fp;
+        double d = f / fp;
+        th -= d;
         if (th < 0.0) th = 0.0;
         if (th > ORC_PI) th = ORC_PI;
+        if (fabs(d) < 1e-15) break;
     }
     return th;
 }

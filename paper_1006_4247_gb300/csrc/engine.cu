@@ -50,6 +50,14 @@ FastDiv make_fastdiv(uint32_t d) {
 
 constexpr int kMaxNT = 512;  // must match the exchange kernels' shared-memory limit
 
+// Sites per thread of the half sweep: 16-byte vectors where the row length
+// L/2 allows them (float4 / double2), else 8-byte, else scalar.
+int vec_width(int hL, bool fp64) {
+    if (!fp64 && hL % 4 == 0) return 4;
+    if (hL % 2 == 0) return 2;
+    return 1;
+}
+
 }  // namespace
 
 struct pt_engine {
@@ -66,13 +74,17 @@ struct pt_engine {
     std::vector<SampleDesc> samples;
     std::vector<ChainDesc> chains;
     std::vector<int4> reps;
-    std::vector<int2> tiles;
+    std::vector<int2> tiles;          // half-sweep tiles, grouped by vector class
+    std::vector<int> q_sample;
     std::vector<long long> chain_off;
     std::vector<float> maxsumJ;       // per sample: max_x sum of |J| over the 6 bonds
     std::vector<float> eps_host;      // last cooling parameters
     size_t pool_elems = 0, J_elems = 0;
     int R = 0, P = 0, T = 0, sumNT = 0, sumEps = 0;
     bool energy_valid = false;
+    int policy = PT_POLICY_AUTO;
+    bool all_resident = false;        // every sample fits the resident kernel
+    int max_half = 0;
     uint64_t step_host = 0;           // mirror of the device step counter
 
     std::vector<void*> owned;
@@ -186,7 +198,7 @@ pt_status run(pt_engine* e, int kind, int n_kernels, F&& launcher) {
     } while (0)
 
 pt_status compute_energy(pt_engine* e) {
-    RUN(PT_KERNEL_ENERGY, 1, launch_energy(e->d, e->fp64, e->stream));
+    RUN(PT_KERNEL_ENERGY, sweep_launch_count(e->d), launch_energy(e->d, e->fp64, e->stream));
     RUN(PT_KERNEL_ENERGY, 1, launch_energy_finalize(e->d, e->stream));
     e->energy_valid = true;
     return PT_OK;
@@ -251,8 +263,9 @@ pt_status create_impl(pt_handle* out, int n_samples, const int* Ls, const int* N
         sd.eps_off = eps_off;
         sd.chain0 = (int)e->chains.size();
         sd.r0 = r;
-        sd.tile0 = t;
-        sd.tiles_per_rep = (half + TILE - 1) / TILE;
+        sd.vec = vec_width(hL, e->fp64);
+        sd.tiles_per_rep = (half + TILE * sd.vec - 1) / (TILE * sd.vec);
+        sd.tile0 = 0;  // set below, once tiles are grouped by class
         // colour-split forward couplings and the invertibility bound
         Jsplit.resize((size_t)(J_off + 3LL * N));
         const float* J = Js[s];
@@ -271,7 +284,10 @@ pt_status create_impl(pt_handle* out, int n_samples, const int* Ls, const int* N
             mx = std::max(mx, sum);
         }
         e->maxsumJ.push_back(mx);
-        for (int b = 0; b < NT; ++b) beta_all.push_back(betas[s][b]);
+        for (int b = 0; b < NT; ++b) {
+            beta_all.push_back(betas[s][b]);
+            e->q_sample.push_back(s);
+        }
         for (int c = 0; c < e->C; ++c) {
             const int ch = (int)e->chains.size();
             e->chains.push_back(ChainDesc{s, c, r, pair});
@@ -279,8 +295,6 @@ pt_status create_impl(pt_handle* out, int n_samples, const int* Ls, const int* N
             pool += (long long)(NT + 2) * 3 * N;
             for (int b = 0; b < NT; ++b) {
                 e->reps.push_back(make_int4(s, ch, b, c * NT + b));
-                for (int k = 0; k < sd.tiles_per_rep; ++k) e->tiles.push_back(make_int2(r, k * TILE));
-                t += sd.tiles_per_rep;
                 ++r;
             }
             pair += NT - 1;
@@ -289,6 +303,31 @@ pt_status create_impl(pt_handle* out, int n_samples, const int* Ls, const int* N
         J_off += 3LL * N;
         beta_off += NT;
         eps_off += NT - 1;
+    }
+    // half-sweep tiles grouped by vector class (widths 4, 2, 1); within a
+    // class sample by sample and replica by replica, so that the tiles of a
+    // replica are contiguous
+    const int widths[3] = {4, 2, 1};
+    for (int cls = 0; cls < 3; ++cls) {
+        e->d.vclass_begin[cls] = t;
+        e->d.vclass_width[cls] = widths[cls];
+        for (int s = 0; s < n_samples; ++s) {
+            SampleDesc& sd = e->samples[s];
+            if (sd.vec != widths[cls]) continue;
+            sd.tile0 = t;
+            const int nrep = e->C * sd.NT;
+            for (int q = 0; q < nrep; ++q)
+                for (int k = 0; k < sd.tiles_per_rep; ++k) {
+                    e->tiles.push_back(make_int2(sd.r0 + q, k * TILE * sd.vec));
+                    ++t;
+                }
+        }
+        e->d.vclass_count[cls] = t - e->d.vclass_begin[cls];
+    }
+    e->all_resident = true;
+    for (const SampleDesc& sd : e->samples) {
+        e->all_resident = e->all_resident && resident_supported(sd, e->fp64);
+        e->max_half = std::max(e->max_half, sd.half);
     }
     e->R = r;
     e->T = t;
@@ -338,14 +377,13 @@ pt_status create_impl(pt_handle* out, int n_samples, const int* Ls, const int* N
     SampleDesc* dS; TRY(upload(e, &dS, e->samples)); d.samples = dS;
     ChainDesc* dC; TRY(upload(e, &dC, e->chains)); d.chains = dC;
     int4* dR; TRY(upload(e, &dR, e->reps)); d.reps = dR;
-    int2* dT; TRY(upload(e, &dT, e->tiles)); d.tiles = dT;
+    int2* dT; TRY(upload(e, &dT, e->tiles)); d.vtiles = dT;
+    int* dQs; TRY(upload(e, &dQs, e->q_sample)); d.q_sample = dQs;
     long long* dO; TRY(upload(e, &dO, e->chain_off)); d.chain_off = dO;
     std::vector<unsigned long long> z1(1, 0ull);
     TRY(upload(e, &d.d_step, z1));
-    std::vector<double> zt((size_t)t, 0.0), zt9((size_t)t * 18, 0.0), zq((size_t)e->sumNT * 9, 0.0),
-        zx((size_t)e->sumNT, 0.0);
+    std::vector<double> zt((size_t)t, 0.0), zq((size_t)e->sumNT * 9, 0.0), zx((size_t)e->sumNT, 0.0);
     TRY(upload(e, &d.part, zt));
-    TRY(upload(e, &d.part9, zt9));
     TRY(upload(e, &d.Q, zq));
     TRY(upload(e, &d.chi, zx));
 #undef TRY
@@ -354,6 +392,7 @@ pt_status create_impl(pt_handle* out, int n_samples, const int* Ls, const int* N
     d.n_chains = (int)e->chains.size();
     d.n_reps = r;
     d.n_tiles = t;
+    d.n_q = e->sumNT;
     d.max_NT = 0;
     for (int v : e->NT) d.max_NT = std::max(d.max_NT, v);
 
@@ -449,16 +488,24 @@ pt_status pt_sweep(pt_handle e, int n_hb, int n_or) {
     if (n_hb < 0 || n_or < 0) return fail(PT_ERR_ARG, "n_hb, n_or must be >= 0");
     const int total = 2 * (n_hb + n_or);
     if (total == 0) return PT_OK;
+    const bool resident = e->policy == PT_POLICY_RESIDENT || (e->policy == PT_POLICY_AUTO && e->all_resident);
+    if (resident) {
+        RUN(PT_KERNEL_RESIDENT, 1, launch_resident(e->d, e->fp64, n_hb, n_or, e->max_half, e->stream));
+        RUN(PT_KERNEL_OTHER, 1, launch_advance_step(e->d, total, e->stream));
+        e->step_host += (uint64_t)total;
+        e->energy_valid = true;
+        return PT_OK;
+    }
     int k = 0;
     for (int hb = 0; hb < n_hb; ++hb)
         for (int c = 0; c < 2; ++c, ++k) {
             const bool last = (k == total - 1);
-            RUN(PT_KERNEL_HB, 1, launch_halfsweep(e->d, e->fp64, 1, last, c, k, e->stream));
+            RUN(PT_KERNEL_HB, sweep_launch_count(e->d), launch_halfsweep(e->d, e->fp64, 1, last, c, k, e->stream));
         }
     for (int o = 0; o < n_or; ++o)
         for (int c = 0; c < 2; ++c, ++k) {
             const bool last = (k == total - 1);
-            RUN(PT_KERNEL_OR, 1, launch_halfsweep(e->d, e->fp64, 0, last, c, k, e->stream));
+            RUN(PT_KERNEL_OR, sweep_launch_count(e->d), launch_halfsweep(e->d, e->fp64, 0, last, c, k, e->stream));
         }
     RUN(PT_KERNEL_ENERGY, 1, launch_energy_finalize(e->d, e->stream));
     RUN(PT_KERNEL_OTHER, 1, launch_advance_step(e->d, total, e->stream));
@@ -497,7 +544,7 @@ pt_status pt_measure(pt_handle e, double* energy, double* overlap, double* chi) 
         pt_status st = compute_energy(e);
         if (st != PT_OK) return st;
     }
-    if (overlap || chi) RUN(PT_KERNEL_MEASURE, 2, launch_overlap(e->d, e->fp64, e->stream));
+    if (overlap || chi) RUN(PT_KERNEL_MEASURE, 1, launch_overlap(e->d, e->fp64, e->stream));
     if (energy) CK(cudaMemcpyAsync(energy, e->d.H, sizeof(double) * e->R, cudaMemcpyDeviceToHost, e->stream));
     if (overlap) CK(cudaMemcpyAsync(overlap, e->d.Q, sizeof(double) * 9 * e->sumNT, cudaMemcpyDeviceToHost, e->stream));
     if (chi) CK(cudaMemcpyAsync(chi, e->d.chi, sizeof(double) * e->sumNT, cudaMemcpyDeviceToHost, e->stream));
@@ -511,7 +558,7 @@ pt_status pt_measure_device(pt_handle e, double* d_energy, double* d_overlap, do
         pt_status st = compute_energy(e);
         if (st != PT_OK) return st;
     }
-    if (e->C == 2) RUN(PT_KERNEL_MEASURE, 2, launch_overlap(e->d, e->fp64, e->stream));
+    if (e->C == 2) RUN(PT_KERNEL_MEASURE, 1, launch_overlap(e->d, e->fp64, e->stream));
     if (d_energy) CK(cudaMemcpyAsync(d_energy, e->d.H, sizeof(double) * e->R, cudaMemcpyDeviceToDevice, e->stream));
     if (d_overlap)
         CK(cudaMemcpyAsync(d_overlap, e->d.Q, sizeof(double) * 9 * e->sumNT, cudaMemcpyDeviceToDevice, e->stream));
@@ -731,6 +778,16 @@ pt_status pt_load(pt_handle e, const char* path) {
     e->step_host = hd.step;
     CK(cudaMemcpy(e->d.d_step, &hd.step, sizeof hd.step, cudaMemcpyHostToDevice));
     e->energy_valid = hd.energy_valid != 0;
+    return PT_OK;
+}
+
+pt_status pt_set_policy(pt_handle e, int policy) {
+    if (!e) return fail(PT_ERR_ARG, "NULL handle");
+    if (policy != PT_POLICY_AUTO && policy != PT_POLICY_STREAMING && policy != PT_POLICY_RESIDENT)
+        return fail(PT_ERR_ARG, "bad policy %d", policy);
+    if (policy == PT_POLICY_RESIDENT && !e->all_resident)
+        return fail(PT_ERR_STATE, "a sample does not fit the resident sweep kernel");
+    e->policy = policy;
     return PT_OK;
 }
 

@@ -24,17 +24,22 @@ struct DevBatch {
     const SampleDesc* samples;      // [S]
     const ChainDesc* chains;        // [chains]
     const int4* reps;               // [R] (sample, chain, b, copy*NT + b)
-    const int2* tiles;              // [T] (replica, first h)
+    const int2* vtiles;             // [T] (replica, first h) of the half-sweep tiles
+    const int* q_sample;            // [sum NT] sample of each (sample, beta) pair
     const long long* chain_off;     // [chains] element offset of buffer 0
     unsigned long long* d_step;     // Philox step counter
     unsigned long long seed;
     double* part;                   // [T] per-tile energy partials
-    double* part9;                  // [2 T][9] per-tile overlap partials
     double* Q;                      // [sum NT][9]
     double* chi;                    // [sum NT]
-    int n_samples, n_chains, n_reps, n_tiles;
+    int n_samples, n_chains, n_reps, n_tiles, n_q;
     int max_NT;
+    // half-sweep tiles are grouped by vector width (sites per thread)
+    int vclass_begin[3], vclass_count[3], vclass_width[3];
 };
+
+// Number of kernels one half sweep launches (one per vector-width class).
+int sweep_launch_count(const DevBatch& b);
 
 // Half sweeps (kind 0 = overrelaxation, 1 = heat bath); `energy` also writes
 // the per-tile energy partials of the updated colour (valid for colour 1).
@@ -46,5 +51,10 @@ cudaError_t launch_init_spins(const DevBatch& b, bool fp64, int ordered, cudaStr
 cudaError_t launch_advance_step(const DevBatch& b, int by, cudaStream_t st);
 cudaError_t launch_overlap(const DevBatch& b, bool fp64, cudaStream_t st);
 cudaError_t launch_exchange(const DevBatch& b, bool fp64, int mode, cudaStream_t st);
+
+// Resident sweep blocks: one CTA per replica runs n_hb + n_or sweeps in shared
+// memory and writes H[r].
+bool resident_supported(const SampleDesc& sd, bool fp64);
+cudaError_t launch_resident(const DevBatch& b, bool fp64, int n_hb, int n_or, int max_half, cudaStream_t st);
 
 }  // namespace ptk

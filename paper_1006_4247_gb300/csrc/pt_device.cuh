@@ -106,7 +106,8 @@ template <> struct M<float> {
     static __device__ __forceinline__ float atan2_(float y, float x) { return atan2f(y, x); }
     static __device__ __forceinline__ float copysign_(float a, float b) { return copysignf(a, b); }
     static constexpr float tinyR = 1e-30f;
-    static constexpr int newton_iters = 6;
+    static constexpr int newton_max = 30;
+    static constexpr float newton_tol = 2e-7f;
     static constexpr float pi = CUDART_PI_F;
 };
 template <> struct M<double> {
@@ -122,7 +123,8 @@ template <> struct M<double> {
     static __device__ __forceinline__ double atan2_(double y, double x) { return atan2(y, x); }
     static __device__ __forceinline__ double copysign_(double a, double b) { return copysign(a, b); }
     static constexpr double tinyR = 1e-280;
-    static constexpr int newton_iters = 8;
+    static constexpr int newton_max = 50;
+    static constexpr double newton_tol = 1e-15;
     static constexpr double pi = CUDART_PI;
 };
 
@@ -273,9 +275,10 @@ __device__ __forceinline__ T cool_site(T eps, const V3<T>& S, V3<T>& s) {
 }
 
 // Heating step = inverse cooling step: theta' given, solve
-// theta - e sin(theta) = theta' (e = eps |S| < 1) by a fixed number of Newton
-// iterations from theta' + e sin(theta'), rotate s' away from S by
-// theta - theta'.  Returns ln det J_f at the pre-image.
+// theta - e sin(theta) = theta' (e = eps |S| < 1) by Newton iterations from
+// theta' + e sin(theta') until the step is below the precision's tolerance
+// (at most newton_max), rotate s' away from S by theta - theta'.  Returns
+// ln det J_f at the pre-image.
 template <typename T>
 __device__ __forceinline__ T heat_site(T eps, const V3<T>& S, V3<T>& s) {
     const T nS = M<T>::sqrt_(dot(S, S));
@@ -285,12 +288,13 @@ __device__ __forceinline__ T heat_site(T eps, const V3<T>& S, V3<T>& s) {
     const T e = eps * nS;
     const T thp = M<T>::atan2_(pn, sS);
     T th = thp + e * M<T>::sin_(thp);
-#pragma unroll
-    for (int it = 0; it < M<T>::newton_iters; ++it) {
+    for (int it = 0; it < M<T>::newton_max; ++it) {
         T sn, cs;
         M<T>::sincos_(th, &sn, &cs);
-        th -= (th - e * sn - thp) / ((T)1 - e * cs);
+        const T d = (th - e * sn - thp) / ((T)1 - e * cs);
+        th -= d;
         th = th < (T)0 ? (T)0 : (th > M<T>::pi ? M<T>::pi : th);
+        if (fabs(d) < M<T>::newton_tol) break;
     }
     const T alpha = th - thp;
     if (pn > (T)0) {
@@ -307,6 +311,39 @@ __device__ __forceinline__ T heat_site(T eps, const V3<T>& S, V3<T>& s) {
     const T al = e * sth;
     const T j = ((T)1 - e * cth) * (M<T>::cos_(al) - e * cth * sinc_(al));
     return M<T>::log_(fabs(j));
+}
+
+// ---------------------------------------------------------------------------
+// Vector loads / stores of V consecutive elements (V * sizeof(T) = 4, 8, 16).
+// ---------------------------------------------------------------------------
+template <typename T, int V> struct VecT;
+template <> struct VecT<float, 1> { using t = float; };
+template <> struct VecT<float, 2> { using t = float2; };
+template <> struct VecT<float, 4> { using t = float4; };
+template <> struct VecT<double, 1> { using t = double; };
+template <> struct VecT<double, 2> { using t = double2; };
+
+template <typename T, int V>
+__device__ __forceinline__ void ldv(const T* __restrict__ p, T (&o)[V]) {
+    const typename VecT<T, V>::t v = *reinterpret_cast<const typename VecT<T, V>::t*>(p);
+    const T* q = reinterpret_cast<const T*>(&v);
+#pragma unroll
+    for (int i = 0; i < V; ++i) o[i] = q[i];
+}
+template <typename T, int V>
+__device__ __forceinline__ void ldv_nc(const T* __restrict__ p, T (&o)[V]) {
+    const typename VecT<T, V>::t v = __ldg(reinterpret_cast<const typename VecT<T, V>::t*>(p));
+    const T* q = reinterpret_cast<const T*>(&v);
+#pragma unroll
+    for (int i = 0; i < V; ++i) o[i] = q[i];
+}
+template <typename T, int V>
+__device__ __forceinline__ void stv(T* __restrict__ p, const T (&o)[V]) {
+    typename VecT<T, V>::t v;
+    T* q = reinterpret_cast<T*>(&v);
+#pragma unroll
+    for (int i = 0; i < V; ++i) q[i] = o[i];
+    *reinterpret_cast<typename VecT<T, V>::t*>(p) = v;
 }
 
 // ---------------------------------------------------------------------------

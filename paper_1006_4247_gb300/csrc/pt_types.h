@@ -35,14 +35,16 @@ struct SampleDesc {
     int eps_off;              // first eps (NT - 1 per sample)
     int chain0;               // first chain of this sample
     int r0;                   // first replica of chain0
-    int tile0;                // first sweep tile of replica r0
-    int tiles_per_rep;        // ceil(half / TILE)
+    int tile0;                // first half-sweep tile of replica r0
+    int tiles_per_rep;        // ceil(half / (TILE * vec))
+    int vec;                  // sites per thread in the half sweep (4, 2 or 1)
+    int pad;
 };
 
 struct ChainDesc {
     int s, copy, r0, pair_off;   // sample, copy, first replica, first pair counter
 };
 
-constexpr int TILE = 256;        // half-sweep tile: 256 sites of one colour of one replica
+constexpr int TILE = 256;        // threads per half-sweep tile (a tile is TILE * vec sites)
 
 }  // namespace ptk

@@ -1,0 +1,181 @@
+// resident.cu -- whole update block (n_hb heat-bath + n_or overrelaxation
+// sweeps, section III.C / section IV of Hasenbusch & Schaefer) of one replica
+// inside one CTA, with the replica held in shared memory.
+//
+// For small lattices a replica fits on chip (L = 16: 4096 sites x 12 B =
+// 48 KB in float), so instead of 2 (n_hb + n_or) passes over HBM the block is
+// read once, all half sweeps run out of shared memory with a CTA barrier
+// between colours, and the result is written once.  The energy of the final
+// configuration is reduced during the last half sweep (every bond has exactly
+// one colour-1 end) and written straight to H[r].
+//
+// Thread mapping inside a half sweep is the one of the streaming kernel
+// (V = 4 consecutive sites of one row per thread, aligned float4 shared-memory
+// loads, +-x neighbours from the same vector shifted by one plus one wrapped
+// element); couplings come from global memory through the read-only cache
+// (one sample's couplings are shared by all its replicas).
+#include "kernels.h"
+#include "pt_device.cuh"
+
+namespace ptk {
+
+constexpr int RES_THREADS = 256;
+
+template <typename T, int V, int KIND>
+__device__ __forceinline__ double res_halfsweep(T* __restrict__ sm, const float* __restrict__ J,
+                                                const SampleDesc& sd, int color, T beta,
+                                                unsigned long long seed, uint32_t sample,
+                                                uint32_t rep_id, unsigned long long step, bool energy) {
+    const int half = sd.half, hL = sd.hL, L = sd.L;
+    T* own = sm + color * 3 * half;
+    const T* oth = sm + (1 - color) * 3 * half;
+    const float* Jown = J + color * 3 * half;
+    const float* Joth = J + (1 - color) * 3 * half;
+    double e = 0.0;
+    for (int h0 = (int)threadIdx.x * V; h0 < half; h0 += RES_THREADS * V) {
+        const int row = (int)fdiv((uint32_t)h0, sd.div_hL);
+        const int ih0 = h0 - row * hL;
+        const int k = (int)fdiv((uint32_t)row, sd.div_L);
+        const int j = row - k * L;
+        const int p = (j + k + color) & 1;
+        const int rb = row * hL;
+        const int xs = p ? rb + ((ih0 + V == hL) ? 0 : ih0 + V) : rb + ((ih0 == 0) ? hL - 1 : ih0 - 1);
+        const int jp = (j + 1 == L) ? 0 : j + 1, jm = (j == 0) ? L - 1 : j - 1;
+        const int kp = (k + 1 == L) ? 0 : k + 1, km = (k == 0) ? L - 1 : k - 1;
+        const int hyp = ih0 + hL * (jp + L * k), hym = ih0 + hL * (jm + L * k);
+        const int hzp = ih0 + hL * (j + L * kp), hzm = ih0 + hL * (j + L * km);
+
+        float jf[3][V], jxb[V], jyb[V], jzb[V];
+        ldv_nc<float, V>(Jown + h0, jf[0]);
+        ldv_nc<float, V>(Jown + half + h0, jf[1]);
+        ldv_nc<float, V>(Jown + 2 * half + h0, jf[2]);
+        {
+            float jx[V];
+            ldv_nc<float, V>(Joth + h0, jx);
+            const float jxs = __ldg(Joth + xs);
+#pragma unroll
+            for (int v = 0; v < V; ++v) jxb[v] = p ? jx[v] : (v == 0 ? jxs : jx[v - 1]);
+        }
+        ldv_nc<float, V>(Joth + half + hym, jyb);
+        ldv_nc<float, V>(Joth + 2 * half + hzm, jzb);
+
+        T S[3][V];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const T* o = oth + c * half;
+            T O[V], Yp[V], Ym[V], Zp[V], Zm[V];
+            ldv<T, V>(o + h0, O);
+            const T os = o[xs];
+            ldv<T, V>(o + hyp, Yp);
+            ldv<T, V>(o + hym, Ym);
+            ldv<T, V>(o + hzp, Zp);
+            ldv<T, V>(o + hzm, Zm);
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const T xp = p ? (v == V - 1 ? os : O[v + 1]) : O[v];
+                const T xm = p ? O[v] : (v == 0 ? os : O[v - 1]);
+                S[c][v] = (T)jf[0][v] * xp + (T)jxb[v] * xm + (T)jf[1][v] * Yp[v] + (T)jyb[v] * Ym[v] +
+                          (T)jf[2][v] * Zp[v] + (T)jzb[v] * Zm[v];
+            }
+        }
+        T s[3][V];
+        if (KIND == 0) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) ldv<T, V>(own + c * half + h0, s[c]);
+        }
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const V3<T> Sv = {S[0][v], S[1][v], S[2][v]};
+            V3<T> sv;
+            if (KIND == 1) {
+                const int x = 2 * (ih0 + v) + p + L * row;
+                const uint4 w = rng_words(seed, sample, (uint32_t)x, rep_id, step, 0u);
+                sv = hb_site<T>(beta, Sv, w.x, w.y);
+            } else {
+                sv = {s[0][v], s[1][v], s[2][v]};
+                or_site(Sv, sv);
+            }
+            s[0][v] = sv.x; s[1][v] = sv.y; s[2][v] = sv.z;
+            if (energy) e -= (double)dot(sv, Sv);
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) stv<T, V>(own + c * half + h0, s[c]);
+    }
+    return e;
+}
+
+// Heat-bath half sweeps (1 of 1 + 5L/4 sweeps) run one site per thread so
+// that the register peak is set by the vectorised overrelaxation path and
+// four CTAs fit on an SM.
+template <typename T, int V>
+__global__ void __launch_bounds__(RES_THREADS, 4) k_resident(DevBatch a, int n_hb, int n_or) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sm = reinterpret_cast<T*>(smem_raw);
+    __shared__ double red[32];
+    const int r = blockIdx.x;
+    const int4 rd = a.reps[r];
+    const SampleDesc& sd = a.samples[rd.x];
+    const int half = sd.half;
+    const int n3 = 6 * half;  // elements of one replica
+    T* g = (T*)a.spins + a.chain_off[rd.y] + (long long)a.bufmap[r] * (long long)n3;
+    // load the replica (16-byte vectors; n3 is a multiple of the vector width)
+    constexpr int VW = 16 / sizeof(T);
+    for (int q = threadIdx.x * VW; q < n3; q += RES_THREADS * VW) {
+        T v[VW];
+        ldv<T, VW>(g + q, v);
+        stv<T, VW>(sm + q, v);
+    }
+    __syncthreads();
+    const float* J = a.J + sd.J_off;
+    const T beta = (T)a.betas[sd.beta_off + rd.z];
+    const unsigned long long step0 = *a.d_step;
+    const int total = 2 * (n_hb + n_or);
+    double e = 0.0;
+    int kstep = 0;
+    for (int hb = 0; hb < n_hb; ++hb)
+        for (int c = 0; c < 2; ++c, ++kstep) {
+            const bool last = kstep == total - 1;
+            e += res_halfsweep<T, 1, 1>(sm, J, sd, c, beta, a.seed, (uint32_t)rd.x, (uint32_t)rd.w,
+                                        step0 + (unsigned long long)kstep, last);
+            __syncthreads();
+        }
+    for (int o = 0; o < n_or; ++o)
+        for (int c = 0; c < 2; ++c, ++kstep) {
+            const bool last = kstep == total - 1;
+            e += res_halfsweep<T, V, 0>(sm, J, sd, c, beta, a.seed, (uint32_t)rd.x, (uint32_t)rd.w, 0ull,
+                                        last);
+            __syncthreads();
+        }
+    for (int q = threadIdx.x * VW; q < n3; q += RES_THREADS * VW) {
+        T v[VW];
+        ldv<T, VW>(sm + q, v);
+        stv<T, VW>(g + q, v);
+    }
+    const double H = block_sum(e, red);
+    if (threadIdx.x == 0) a.H[r] = H;
+}
+
+size_t resident_smem_bytes(int half, bool fp64) { return (size_t)6 * half * (fp64 ? 8 : 4); }
+
+bool resident_supported(const SampleDesc& sd, bool fp64) {
+    // float4 / double2 rows and at most 100 KB of spins per CTA (two CTAs per SM)
+    const int V = fp64 ? 2 : 4;
+    return sd.hL % V == 0 && resident_smem_bytes(sd.half, fp64) <= 100 * 1024;
+}
+
+cudaError_t launch_resident(const DevBatch& b, bool fp64, int n_hb, int n_or, int max_half, cudaStream_t st) {
+    const size_t smem = resident_smem_bytes(max_half, fp64);
+    cudaError_t e;
+    if (fp64) {
+        e = cudaFuncSetAttribute(k_resident<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_resident<double, 2><<<b.n_reps, RES_THREADS, smem, st>>>(b, n_hb, n_or);
+    } else {
+        e = cudaFuncSetAttribute(k_resident<float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_resident<float, 4><<<b.n_reps, RES_THREADS, smem, st>>>(b, n_hb, n_or);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace ptk

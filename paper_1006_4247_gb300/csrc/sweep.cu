@@ -2,71 +2,118 @@
 // section III.C of Hasenbusch & Schaefer), the energy reduction, initial
 // spins and the overlap reduction (section II).
 //
-// One thread updates one site of one colour of one replica; a block is a
-// tile of 256 consecutive sites (h) of one replica, so all loads and stores of
-// a warp are unit-stride in the colour-split layout.  The HB kernel reads only
-// the neighbours and writes the site (24 B per update in float); OR also reads
-// the old spin (36 B).
+// Half sweep: one thread updates V consecutive sites (ih0 .. ih0+V-1) of one
+// row (j, k) of one colour of one replica; a block is a tile of 256 V
+// consecutive sites (h) of one replica.  Along a row the checkerboard offset
+// p = (j + k + colour) & 1 is fixed, so the +-x neighbours of the V sites are
+// the aligned vector of the other colour at the same h shifted by one place,
+// plus one element that wraps around the row; the +-y and +-z neighbours and
+// all couplings are aligned vectors.  Per update that is about 7 memory
+// instructions instead of 27, all of them unit-stride across the warp.
+// Heat bath reads only the neighbours (24 B per update in float), the
+// overrelaxation also the old spin (36 B).
 #include "kernels.h"
 #include "pt_device.cuh"
 
 namespace ptk {
 
-template <typename T, int KIND, bool ENERGY>
-__global__ void __launch_bounds__(TILE) k_halfsweep(DevBatch a, int color, int step_k) {
+// KIND 0: overrelaxation, 1: heat bath, 2: energy only (colour 0, no store).
+template <typename T, int V, int KIND, bool ENERGY>
+__global__ void __launch_bounds__(TILE) k_sweep(DevBatch a, int tile_begin, int color, int step_k) {
     __shared__ double sh[32];
-    const int2 tl = a.tiles[blockIdx.x];
+    const int t = tile_begin + (int)blockIdx.x;
+    const int2 tl = a.vtiles[t];
     const int4 rd = a.reps[tl.x];
     const SampleDesc& sd = a.samples[rd.x];
-    const int half = sd.half;
-    const int h = tl.y + (int)threadIdx.x;
-    T* base = (T*)a.spins + a.chain_off[rd.y] + (long long)a.bufmap[tl.x] * (6LL * half);
-    T* own = base + color * 3 * half;
-    const T* oth = base + (1 - color) * 3 * half;
-    const float* Jown = a.J + sd.J_off + color * 3 * half;
-    const float* Joth = a.J + sd.J_off + (1 - color) * 3 * half;
+    const int half = sd.half, hL = sd.hL, L = sd.L;
+    const int h0 = tl.y + (int)threadIdx.x * V;
     double e = 0.0;
-    if (h < half) {
-        const Site st = site_of(sd, color, h);
-        const V3<T> S = local_field<T>(st, half, oth, Jown, Joth);
-        V3<T> s;
-        if (KIND == 1) {
-            const T beta = (T)a.betas[sd.beta_off + rd.z];
-            const unsigned long long step = *a.d_step + (unsigned long long)step_k;
-            const uint4 w = rng_words(a.seed, (uint32_t)rd.x, (uint32_t)st.x, (uint32_t)rd.w, step, 0u);
-            s = hb_site<T>(beta, S, w.x, w.y);
-        } else {
-            s = ld3(own, half, h);
-            or_site(S, s);
-        }
-        st3(own, half, h, s);
-        if (ENERGY) e = -(double)dot(s, S);
-    }
-    if (ENERGY) {
-        const double tot = block_sum(e, sh);
-        if (threadIdx.x == 0) a.part[blockIdx.x] = tot;
-    }
-}
+    if (h0 < half) {
+        T* base = (T*)a.spins + a.chain_off[rd.y] + (long long)a.bufmap[tl.x] * (6LL * half);
+        T* own = base + color * 3 * half;
+        const T* oth = base + (1 - color) * 3 * half;
+        const float* Jown = a.J + sd.J_off + color * 3 * half;
+        const float* Joth = a.J + sd.J_off + (1 - color) * 3 * half;
+        const int row = (int)fdiv((uint32_t)h0, sd.div_hL);
+        const int ih0 = h0 - row * hL;
+        const int k = (int)fdiv((uint32_t)row, sd.div_L);
+        const int j = row - k * L;
+        const int p = (j + k + color) & 1;
+        const int rb = row * hL;
+        // index of the wrapped x neighbour: p = 0 -> left of ih0, p = 1 -> right of ih0+V-1
+        const int xs = p ? rb + ((ih0 + V == hL) ? 0 : ih0 + V) : rb + ((ih0 == 0) ? hL - 1 : ih0 - 1);
+        const int jp = (j + 1 == L) ? 0 : j + 1, jm = (j == 0) ? L - 1 : j - 1;
+        const int kp = (k + 1 == L) ? 0 : k + 1, km = (k == 0) ? L - 1 : k - 1;
+        const int hyp = ih0 + hL * (jp + L * k), hym = ih0 + hL * (jm + L * k);
+        const int hzp = ih0 + hL * (j + L * kp), hzm = ih0 + hL * (j + L * km);
 
-// H = - sum over colour-0 sites of s_x . S_x (every bond has one colour-0 end).
-template <typename T>
-__global__ void __launch_bounds__(TILE) k_energy(DevBatch a) {
-    __shared__ double sh[32];
-    const int2 tl = a.tiles[blockIdx.x];
-    const int4 rd = a.reps[tl.x];
-    const SampleDesc& sd = a.samples[rd.x];
-    const int half = sd.half;
-    const int h = tl.y + (int)threadIdx.x;
-    const T* base = (const T*)a.spins + a.chain_off[rd.y] + (long long)a.bufmap[tl.x] * (6LL * half);
-    double e = 0.0;
-    if (h < half) {
-        const Site st = site_of(sd, 0, h);
-        const V3<T> S = local_field<T>(st, half, base + 3 * half, a.J + sd.J_off, a.J + sd.J_off + 3 * half);
-        const V3<T> s = ld3(base, half, h);
-        e = -(double)dot(s, S);
+        // couplings
+        float jf[3][V], jxb[V], jyb[V], jzb[V];
+        ldv_nc<float, V>(Jown + h0, jf[0]);
+        ldv_nc<float, V>(Jown + half + h0, jf[1]);
+        ldv_nc<float, V>(Jown + 2 * half + h0, jf[2]);
+        {
+            float jx[V];
+            ldv_nc<float, V>(Joth + h0, jx);
+            const float jxs = __ldg(Joth + xs);
+#pragma unroll
+            for (int v = 0; v < V; ++v) jxb[v] = p ? jx[v] : (v == 0 ? jxs : jx[v - 1]);
+        }
+        ldv_nc<float, V>(Joth + half + hym, jyb);
+        ldv_nc<float, V>(Joth + 2 * half + hzm, jzb);
+
+        // neighbour field, component by component
+        T S[3][V];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const T* o = oth + c * half;
+            T O[V], Yp[V], Ym[V], Zp[V], Zm[V];
+            ldv<T, V>(o + h0, O);
+            const T os = o[xs];
+            ldv<T, V>(o + hyp, Yp);
+            ldv<T, V>(o + hym, Ym);
+            ldv<T, V>(o + hzp, Zp);
+            ldv<T, V>(o + hzm, Zm);
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const T xp = p ? (v == V - 1 ? os : O[v + 1]) : O[v];
+                const T xm = p ? O[v] : (v == 0 ? os : O[v - 1]);
+                S[c][v] = (T)jf[0][v] * xp + (T)jxb[v] * xm + (T)jf[1][v] * Yp[v] + (T)jyb[v] * Ym[v] +
+                          (T)jf[2][v] * Zp[v] + (T)jzb[v] * Zm[v];
+            }
+        }
+
+        T s[3][V];
+        if (KIND != 1) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) ldv<T, V>(own + c * half + h0, s[c]);
+        }
+        const T beta = (KIND == 1) ? (T)a.betas[sd.beta_off + rd.z] : (T)0;
+        const unsigned long long step = (KIND == 1) ? *a.d_step + (unsigned long long)step_k : 0ull;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const V3<T> Sv = {S[0][v], S[1][v], S[2][v]};
+            V3<T> sv;
+            if (KIND == 1) {
+                const int x = 2 * (ih0 + v) + p + L * row;
+                const uint4 w = rng_words(a.seed, (uint32_t)rd.x, (uint32_t)x, (uint32_t)rd.w, step, 0u);
+                sv = hb_site<T>(beta, Sv, w.x, w.y);
+            } else {
+                sv = {s[0][v], s[1][v], s[2][v]};
+                if (KIND == 0) or_site(Sv, sv);
+            }
+            s[0][v] = sv.x; s[1][v] = sv.y; s[2][v] = sv.z;
+            if (ENERGY || KIND == 2) e -= (double)dot(sv, Sv);
+        }
+        if (KIND != 2) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) stv<T, V>(own + c * half + h0, s[c]);
+        }
     }
-    const double tot = block_sum(e, sh);
-    if (threadIdx.x == 0) a.part[blockIdx.x] = tot;
+    if (ENERGY || KIND == 2) {
+        const double tot = block_sum(e, sh);
+        if (threadIdx.x == 0) a.part[t] = tot;
+    }
 }
 
 // H[r] = sum of the tile partials of replica r, in tile order.
@@ -83,114 +130,146 @@ __global__ void k_energy_finalize(DevBatch a) {
 
 // Initial spins: uniform on the sphere from Philox purpose 4
 // (z = (w0 >> 8) 2^-23 - 1, phi = 2 pi (w1 >> 8) 2^-24), or all (1, 0, 0).
+// Grid: (replica, colour); threads stride over the sites of the colour.
 template <typename T>
 __global__ void __launch_bounds__(TILE) k_init_spins(DevBatch a, int ordered) {
-    const int color = blockIdx.y;
-    const int2 tl = a.tiles[blockIdx.x];
-    const int4 rd = a.reps[tl.x];
+    const int r = blockIdx.x, color = blockIdx.y;
+    const int4 rd = a.reps[r];
     const SampleDesc& sd = a.samples[rd.x];
     const int half = sd.half;
-    const int h = tl.y + (int)threadIdx.x;
-    if (h >= half) return;
-    T* base = (T*)a.spins + a.chain_off[rd.y] + (long long)a.bufmap[tl.x] * (6LL * half);
-    T* own = base + color * 3 * half;
-    V3<T> s;
-    if (ordered) {
-        s.x = (T)1; s.y = (T)0; s.z = (T)0;
-    } else {
-        const Site st = site_of(sd, color, h);
-        const uint4 w = rng_words(a.seed, (uint32_t)rd.x, (uint32_t)st.x, (uint32_t)rd.w, 0ull, 4u);
-        const T z = (T)(w.x >> 8) * (T)0x1p-23 - (T)1;
-        const T phi = (T)2 * M<T>::pi * ((T)(w.y >> 8) * (T)0x1p-24);
-        const T rho = M<T>::sqrt_((T)1 - z * z);
-        T sp, cp;
-        M<T>::sincos_(phi, &sp, &cp);
-        s.x = rho * cp; s.y = rho * sp; s.z = z;
+    T* own = (T*)a.spins + a.chain_off[rd.y] + (long long)a.bufmap[r] * (6LL * half) + color * 3 * half;
+    for (int h = threadIdx.x; h < half; h += blockDim.x) {
+        V3<T> s;
+        if (ordered) {
+            s.x = (T)1; s.y = (T)0; s.z = (T)0;
+        } else {
+            const Site st = site_of(sd, color, h);
+            const uint4 w = rng_words(a.seed, (uint32_t)rd.x, (uint32_t)st.x, (uint32_t)rd.w, 0ull, 4u);
+            const T z = (T)(w.x >> 8) * (T)0x1p-23 - (T)1;
+            const T phi = (T)2 * M<T>::pi * ((T)(w.y >> 8) * (T)0x1p-24);
+            const T rho = M<T>::sqrt_((T)1 - z * z);
+            T sp, cp;
+            M<T>::sincos_(phi, &sp, &cp);
+            s.x = rho * cp; s.y = rho * sp; s.z = z;
+        }
+        st3(own, half, h, s);
     }
-    st3(own, half, h, s);
 }
 
 __global__ void k_advance_step(unsigned long long* d_step, int by) { *d_step += (unsigned long long)by; }
 
 // Overlap Q_ab = sum_x s0_a,x s1_b,x between copy 0 and copy 1 at the same
-// beta index (Eq. over).  Grid: (tiles, colour); tiles of copy-1 replicas exit.
+// beta index (Eq. over) and chi = (1/N) sum_ab Q_ab^2.  One block per
+// (sample, beta index); each thread accumulates its sites in T in chunks of
+// at most 32 sites, then in double; warp shuffles and one shared-memory pass
+// finish the nine sums in a fixed order.
 template <typename T>
 __global__ void __launch_bounds__(TILE) k_overlap(DevBatch a) {
-    __shared__ double sh[32];
-    const int color = blockIdx.y;
-    const int2 tl = a.tiles[blockIdx.x];
-    const int4 rd = a.reps[tl.x];
-    const ChainDesc cd = a.chains[rd.y];
-    if (cd.copy != 0) return;
-    const SampleDesc& sd = a.samples[rd.x];
+    __shared__ double sh[9][TILE / 32];
+    const int q = blockIdx.x;  // beta_off(s) + b over all samples
+    const int s = a.q_sample[q];
+    const SampleDesc& sd = a.samples[s];
+    const int b = q - sd.beta_off;
     const int half = sd.half;
-    const int r1 = tl.x + sd.NT;  // same beta index in copy 1
-    const int h = tl.y + (int)threadIdx.x;
-    const T* b0 = (const T*)a.spins + a.chain_off[rd.y] + (long long)a.bufmap[tl.x] * (6LL * half) + color * 3 * half;
-    const T* b1 = (const T*)a.spins + a.chain_off[rd.y + 1] + (long long)a.bufmap[r1] * (6LL * half) + color * 3 * half;
-    V3<T> s0 = {(T)0, (T)0, (T)0}, s1 = {(T)0, (T)0, (T)0};
-    if (h < half) {
-        s0 = ld3(b0, half, h);
-        s1 = ld3(b1, half, h);
+    const int r0 = sd.r0 + b, r1 = sd.r0 + sd.NT + b;
+    const T* b0 = (const T*)a.spins + a.chain_off[sd.chain0] + (long long)a.bufmap[r0] * (6LL * half);
+    const T* b1 = (const T*)a.spins + a.chain_off[sd.chain0 + 1] + (long long)a.bufmap[r1] * (6LL * half);
+    double acc[9];
+#pragma unroll
+    for (int n = 0; n < 9; ++n) acc[n] = 0.0;
+    const int N = 2 * half;
+    for (int base = 0; base < N; base += 32 * TILE) {
+        T part[9];
+#pragma unroll
+        for (int n = 0; n < 9; ++n) part[n] = (T)0;
+        const int end = min(N, base + 32 * TILE);
+        for (int x = base + (int)threadIdx.x; x < end; x += TILE) {
+            const int c = x >= half ? 1 : 0;
+            const int h = x - c * half;
+            const T* p0 = b0 + c * 3 * half + h;
+            const T* p1 = b1 + c * 3 * half + h;
+            const T u0[3] = {p0[0], p0[half], p0[2 * half]};
+            const T u1[3] = {p1[0], p1[half], p1[2 * half]};
+#pragma unroll
+            for (int n = 0; n < 9; ++n) part[n] += u0[n / 3] * u1[n % 3];
+        }
+#pragma unroll
+        for (int n = 0; n < 9; ++n) acc[n] += (double)part[n];
     }
-    const T u0[3] = {s0.x, s0.y, s0.z};
-    const T u1[3] = {s1.x, s1.y, s1.z};
-    double* out = a.part9 + ((long long)blockIdx.x * 2 + color) * 9;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int n = 0; n < 9; ++n) {
-        const double v = block_sum((double)(u0[n / 3] * u1[n % 3]), sh);
-        if (threadIdx.x == 0) out[n] = v;
+        const double v = warp_sum(acc[n]);
+        if (lane == 0) sh[n][wid] = v;
     }
-}
-
-// Q[beta_off + b][9] and chi = (1/N) sum Q^2 from the tile partials.
-__global__ void k_overlap_finalize(DevBatch a) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= a.n_reps) return;
-    const int4 rd = a.reps[r];
-    const ChainDesc cd = a.chains[rd.y];
-    if (cd.copy != 0) return;
-    const SampleDesc& sd = a.samples[rd.x];
-    const int t0 = sd.tile0 + (r - sd.r0) * sd.tiles_per_rep;
-    const int q = sd.beta_off + rd.z;
-    double chi = 0.0;
-    for (int n = 0; n < 9; ++n) {
-        double v = 0.0;
-        for (int c = 0; c < 2; ++c)
-            for (int k = 0; k < sd.tiles_per_rep; ++k) v += a.part9[((long long)(t0 + k) * 2 + c) * 9 + n];
-        a.Q[(long long)q * 9 + n] = v;
-        chi += v * v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double chi = 0.0;
+        for (int n = 0; n < 9; ++n) {
+            double v = (lane < TILE / 32) ? sh[n][lane] : 0.0;
+            v = warp_sum(v);
+            if (lane == 0) {
+                a.Q[(long long)q * 9 + n] = v;
+                chi += v * v;
+            }
+        }
+        if (lane == 0) a.chi[q] = chi / (double)N;
     }
-    a.chi[q] = chi / (2.0 * (double)sd.half);
 }
 
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
-template <typename T>
-static cudaError_t halfsweep_t(const DevBatch& b, int kind, bool energy, int color, int step_k,
-                               cudaStream_t st) {
-    dim3 grid(b.n_tiles), block(TILE);
+template <typename T, int V>
+static void sweep_tv(const DevBatch& b, int kind, bool energy, int color, int step_k, int begin, int count,
+                     cudaStream_t st) {
+    if (count == 0) return;
+    dim3 grid(count), block(TILE);
     if (kind == 1) {
-        if (energy) k_halfsweep<T, 1, true><<<grid, block, 0, st>>>(b, color, step_k);
-        else k_halfsweep<T, 1, false><<<grid, block, 0, st>>>(b, color, step_k);
+        if (energy) k_sweep<T, V, 1, true><<<grid, block, 0, st>>>(b, begin, color, step_k);
+        else k_sweep<T, V, 1, false><<<grid, block, 0, st>>>(b, begin, color, step_k);
+    } else if (kind == 0) {
+        if (energy) k_sweep<T, V, 0, true><<<grid, block, 0, st>>>(b, begin, color, step_k);
+        else k_sweep<T, V, 0, false><<<grid, block, 0, st>>>(b, begin, color, step_k);
     } else {
-        if (energy) k_halfsweep<T, 0, true><<<grid, block, 0, st>>>(b, color, step_k);
-        else k_halfsweep<T, 0, false><<<grid, block, 0, st>>>(b, color, step_k);
+        k_sweep<T, V, 2, false><<<grid, block, 0, st>>>(b, begin, 0, 0);
     }
-    return cudaGetLastError();
 }
 
-cudaError_t launch_halfsweep(const DevBatch& b, bool fp64, int kind, bool energy, int color,
-                             int step_k, cudaStream_t st) {
-    return fp64 ? halfsweep_t<double>(b, kind, energy, color, step_k, st)
-                : halfsweep_t<float>(b, kind, energy, color, step_k, st);
+// One launch per vector-width class present in the batch.
+static cudaError_t sweep_all(const DevBatch& b, bool fp64, int kind, bool energy, int color, int step_k,
+                             cudaStream_t st) {
+    for (int cls = 0; cls < 3; ++cls) {
+        const int begin = b.vclass_begin[cls], count = b.vclass_count[cls];
+        if (count == 0) continue;
+        const int V = b.vclass_width[cls];
+        if (fp64) {
+            if (V == 2) sweep_tv<double, 2>(b, kind, energy, color, step_k, begin, count, st);
+            else sweep_tv<double, 1>(b, kind, energy, color, step_k, begin, count, st);
+        } else {
+            if (V == 4) sweep_tv<float, 4>(b, kind, energy, color, step_k, begin, count, st);
+            else if (V == 2) sweep_tv<float, 2>(b, kind, energy, color, step_k, begin, count, st);
+            else sweep_tv<float, 1>(b, kind, energy, color, step_k, begin, count, st);
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+int sweep_launch_count(const DevBatch& b) {
+    int n = 0;
+    for (int cls = 0; cls < 3; ++cls) n += b.vclass_count[cls] > 0;
+    return n;
+}
+
+cudaError_t launch_halfsweep(const DevBatch& b, bool fp64, int kind, bool energy, int color, int step_k,
+                             cudaStream_t st) {
+    return sweep_all(b, fp64, kind, energy, color, step_k, st);
 }
 
 cudaError_t launch_energy(const DevBatch& b, bool fp64, cudaStream_t st) {
-    if (fp64) k_energy<double><<<b.n_tiles, TILE, 0, st>>>(b);
-    else k_energy<float><<<b.n_tiles, TILE, 0, st>>>(b);
-    return cudaGetLastError();
+    return sweep_all(b, fp64, 2, false, 0, 0, st);
 }
 
 cudaError_t launch_energy_finalize(const DevBatch& b, cudaStream_t st) {
@@ -199,7 +278,7 @@ cudaError_t launch_energy_finalize(const DevBatch& b, cudaStream_t st) {
 }
 
 cudaError_t launch_init_spins(const DevBatch& b, bool fp64, int ordered, cudaStream_t st) {
-    dim3 grid(b.n_tiles, 2);
+    dim3 grid(b.n_reps, 2);
     if (fp64) k_init_spins<double><<<grid, TILE, 0, st>>>(b, ordered);
     else k_init_spins<float><<<grid, TILE, 0, st>>>(b, ordered);
     return cudaGetLastError();
@@ -211,12 +290,8 @@ cudaError_t launch_advance_step(const DevBatch& b, int by, cudaStream_t st) {
 }
 
 cudaError_t launch_overlap(const DevBatch& b, bool fp64, cudaStream_t st) {
-    dim3 grid(b.n_tiles, 2);
-    if (fp64) k_overlap<double><<<grid, TILE, 0, st>>>(b);
-    else k_overlap<float><<<grid, TILE, 0, st>>>(b);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    k_overlap_finalize<<<(b.n_reps + 127) / 128, 128, 0, st>>>(b);
+    if (fp64) k_overlap<double><<<b.n_q, TILE, 0, st>>>(b);
+    else k_overlap<float><<<b.n_q, TILE, 0, st>>>(b);
     return cudaGetLastError();
 }
 

@@ -35,9 +35,11 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 ENTRY_POINTS = ["pt_options_default", "pt_create", "pt_create_batch", "pt_sweep", "pt_exchange",
                 "pt_measure", "pt_measure_device", "pt_get_stats", "pt_get_spins", "pt_set_spins",
                 "pt_set_params", "pt_set_rng_step", "pt_get_rng_step", "pt_save", "pt_load",
-                "pt_profile", "pt_profile_read", "pt_destroy", "pt_last_error"]
-PT_KERNEL_KINDS = 6
-KERNEL_KINDS = ["hb", "or", "energy", "exchange", "measure", "other"]
+                "pt_profile", "pt_profile_read", "pt_set_policy", "pt_destroy", "pt_last_error"]
+PT_KERNEL_KINDS = 7
+KERNEL_KINDS = ["hb", "or", "energy", "exchange", "measure", "other", "resident"]
+PT_POLICY_AUTO, PT_POLICY_STREAMING, PT_POLICY_RESIDENT = 0, 1, 2
+POLICIES = {"auto": 0, "streaming": 1, "resident": 2}
 
 
 class PtOptions(C.Structure):
@@ -78,6 +80,7 @@ def load_library(path: str = LIB_PATH):
                 "pt_measure_device": (ip, [vp, vp, vp, vp]),
                 "pt_profile": (ip, [vp, ip]),
                 "pt_profile_read": (ip, [vp, dp, i64p]),
+                "pt_set_policy": (ip, [vp, ip]),
                 "pt_get_stats": (ip, [vp, i64p, i64p, i64p, i32p]),
                 "pt_get_spins": (ip, [vp, ip, ip, ip, dp]),
                 "pt_set_spins": (ip, [vp, ip, ip, ip, dp]),
@@ -174,6 +177,11 @@ def pt_profile_read(h):
     n = np.zeros(PT_KERNEL_KINDS, np.int64)
     _check(load_library().pt_profile_read(h, _ptr(ms, C.c_double), _ptr(n, C.c_int64)))
     return dict(zip(KERNEL_KINDS, ms.tolist())), dict(zip(KERNEL_KINDS, n.tolist()))
+
+
+def pt_set_policy(h, policy):
+    policy = POLICIES.get(policy, policy) if isinstance(policy, str) else int(policy)
+    _check(load_library().pt_set_policy(h, policy))
 
 
 def pt_get_stats(h, proposals=None, accepts=None, round_trips=None, perm=None):
@@ -320,6 +328,9 @@ class Engine:
         chi = np.zeros(n) if self.C == 2 else None
         pt_measure(self.h, H, Q, chi)
         return H, Q, chi
+
+    def set_policy(self, policy):
+        pt_set_policy(self.h, policy)
 
     def measure_device(self):
         pt_measure_device(self.h)

@@ -248,3 +248,62 @@ def test_uneven_batch_parity():
             assert abs(chi[qoff] - chir) <= 1e-10 * max(1, chir)
             qoff += 1
     eng.close()
+
+
+@pytest.mark.parametrize("L", [8, 16])
+def test_resident_and_streaming_paths_fp64(L):
+    """A block of 1 heat-bath + 3 overrelaxation sweeps through the
+    shared-memory resident kernel and through the streaming half sweeps gives
+    the oracle's configuration (1e-12) and the same energies."""
+    S, C, NT, seed = 2, 2, 3, 61
+    res = {}
+    for policy in ("resident", "streaming"):
+        eng, J, B = make_engine(L, S, NT, C, "fp64", seed=seed)
+        eng.set_policy(policy)
+        st = set_random_state(eng, S, C, NT, L, seed=7)
+        step0 = 4242
+        eng.step = step0
+        eng.profile(True)
+        eng.sweep(1, 3)
+        ms, n = eng.profile_read()
+        assert (n["resident"] > 0) == (policy == "resident")
+        out = get_state(eng, S, C, NT)
+        H = eng.energies()
+        for s in range(S):
+            for c in range(C):
+                for b in range(NT):
+                    ref = _oracle_sweep(L, J[s], st[s, c, b], B[s, b], "hb", seed, s, c * NT + b, step0)
+                    for _ in range(3):
+                        ref = _oracle_sweep(L, J[s], ref, B[s, b], "or", seed, s, 0, 0)
+                    # four sweeps: 1e-12 per sweep grows through the chaotic updates
+                    assert np.abs(out[s, c, b] - ref).max() <= 1e-11, (policy, s, c, b)
+                    Hr = orc.energy(L, J[s], out[s, c, b])
+                    assert abs(H[s, c, b] - Hr) <= 1e-11 * max(1, abs(Hr))
+        assert eng.step == step0 + 8
+        res[policy] = out
+        eng.close()
+    assert np.abs(res["resident"] - res["streaming"]).max() <= 1e-14
+
+
+def test_resident_and_streaming_paths_fp32():
+    L, S, C, NT, seed = 16, 2, 2, 3, 63
+    res = {}
+    for policy in ("resident", "streaming"):
+        eng, J, B = make_engine(L, S, NT, C, "fp32", seed=seed)
+        eng.set_policy(policy)
+        set_random_state(eng, S, C, NT, L, seed=8)
+        eng.sweep(1, 2)
+        res[policy] = (get_state(eng, S, C, NT), eng.energies())
+        eng.close()
+    assert np.abs(res["resident"][0] - res["streaming"][0]).max() <= 1e-6
+    assert np.abs(res["resident"][1] - res["streaming"][1]).max() <= 1e-3
+
+
+def test_policy_errors():
+    from paper_1006_4247_gb300 import pt
+    eng, J, B = make_engine(12, 1, 3, 2, "fp32")
+    with pytest.raises(pt.PtError) as ei:
+        eng.set_policy("resident")
+    assert ei.value.status == pt.PT_ERR_STATE
+    eng.set_policy("streaming")
+    eng.close()

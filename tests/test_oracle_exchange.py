@@ -198,7 +198,7 @@ def test_cool_site_jacobian_vs_finite_difference(orc, rng):
 
 
 def test_kepler_newton_converges(orc):
-    for e in np.linspace(0, 0.9, 10):
+    for e in list(np.linspace(0, 0.9, 10)) + [0.97, 0.99, 0.999]:
         for thp in np.linspace(0, np.pi, 41):
             th = orc.kepler_solve(e, thp)
             assert abs(th - e * np.sin(th) - thp) < 1e-13
