@@ -219,6 +219,38 @@ pt_status pt_profile_read(pt_handle h, double *ms, int64_t *launches);
 typedef enum { PT_POLICY_AUTO = 0, PT_POLICY_STREAMING = 1, PT_POLICY_RESIDENT = 2 } pt_policy;
 pt_status pt_set_policy(pt_handle h, int policy);
 
+/* Energies H = -sum_<xy> J_xy s_x . s_y of configurations that live in the
+ * caller's own device memory, computed without allocating any memory.
+ * For callers that cannot let a library call cudaMalloc: code embedded in
+ * another framework whose memory pool must account for every device byte,
+ * and latency-critical loops that forbid allocation after start-up (cudaMalloc
+ * may synchronise the device and has no bounded latency).  The paper has no
+ * counterpart; this is a service of the library, not a step of the method.
+ *   d_spins      device, n_configs configurations, each [L^3][3] in natural
+ *                site order, float (PT_FP32) or double (PT_FP64)
+ *   precision    PT_FP32 or PT_FP64, the element type of d_spins
+ *   L            lattice size, 2 <= L <= 512 (natural order: odd L allowed)
+ *   n_configs    number of configurations, >= 0
+ *   d_couplings  device float [3][L^3], J[mu][x] of bond (x, x + e_mu),
+ *                shared by all configurations
+ *   d_energy     device double [n_configs], written (sums in double)
+ *   stream       cudaStream_t to enqueue on (NULL: legacy stream); the call
+ *                does not synchronise
+ * Scratch: the partial sums live in one fixed array of 65536 doubles
+ * (512 KiB) in the library's device image, which every GPU that loads the
+ * library holds until the process exits.  A call needs
+ * n_configs * ceil(L^3 / 2048) entries (at most 32768 configurations at
+ * L = 16, 4096 at L = 32); larger requests return PT_ERR_ARG and do nothing.
+ * Every call writes each entry it reads, so no clearing is needed, but all
+ * calls share the array: calls that overlap on the GPU (other streams or
+ * other host threads on the same device) race, and the caller must order
+ * them.  The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Errors: PT_ERR_ARG for bad arguments,
+ * PT_ERR_CUDA for a failed launch (text in pt_last_error). */
+pt_status pt_energy_noalloc(const void *d_spins, int precision, int L, int n_configs,
+                            const float *d_couplings, double *d_energy, void *stream);
+
 /* Release all device memory of the handle.  NULL is accepted. */
 pt_status pt_destroy(pt_handle h);
 

@@ -60,6 +60,8 @@ int vec_width(int hL, bool fp64) {
 
 }  // namespace
 
+void ptk::set_last_error(const char* msg) { snprintf(g_err, sizeof g_err, "%s", msg); }
+
 struct pt_engine {
     int S = 0, C = 0;
     bool fp64 = false;

@@ -38,6 +38,9 @@ struct DevBatch {
     int vclass_begin[3], vclass_count[3], vclass_width[3];
 };
 
+// Record the text returned by pt_last_error() for the calling thread.
+void set_last_error(const char* msg);
+
 // Number of kernels one half sweep launches (one per vector-width class).
 int sweep_launch_count(const DevBatch& b);
 

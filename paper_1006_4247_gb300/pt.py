@@ -35,7 +35,8 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 ENTRY_POINTS = ["pt_options_default", "pt_create", "pt_create_batch", "pt_sweep", "pt_exchange",
                 "pt_measure", "pt_measure_device", "pt_get_stats", "pt_get_spins", "pt_set_spins",
                 "pt_set_params", "pt_set_rng_step", "pt_get_rng_step", "pt_save", "pt_load",
-                "pt_profile", "pt_profile_read", "pt_set_policy", "pt_destroy", "pt_last_error"]
+                "pt_profile", "pt_profile_read", "pt_set_policy", "pt_energy_noalloc", "pt_destroy",
+                "pt_last_error"]
 PT_KERNEL_KINDS = 7
 KERNEL_KINDS = ["hb", "or", "energy", "exchange", "measure", "other", "resident"]
 PT_POLICY_AUTO, PT_POLICY_STREAMING, PT_POLICY_RESIDENT = 0, 1, 2
@@ -81,6 +82,7 @@ def load_library(path: str = LIB_PATH):
                 "pt_profile": (ip, [vp, ip]),
                 "pt_profile_read": (ip, [vp, dp, i64p]),
                 "pt_set_policy": (ip, [vp, ip]),
+                "pt_energy_noalloc": (ip, [vp, ip, ip, ip, vp, vp, vp]),
                 "pt_get_stats": (ip, [vp, i64p, i64p, i64p, i32p]),
                 "pt_get_spins": (ip, [vp, ip, ip, ip, dp]),
                 "pt_set_spins": (ip, [vp, ip, ip, ip, dp]),
@@ -182,6 +184,15 @@ def pt_profile_read(h):
 def pt_set_policy(h, policy):
     policy = POLICIES.get(policy, policy) if isinstance(policy, str) else int(policy)
     _check(load_library().pt_set_policy(h, policy))
+
+
+def pt_energy_noalloc(d_spins, precision, L, n_configs, d_couplings, d_energy, stream=None):
+    """Energies of n_configs configurations in caller-owned device memory
+    (integer device pointers), without any allocation by the library; see
+    include/pt.h for the layout, the scratch limit and the ordering rules."""
+    precision = PT_FP64 if precision in ("fp64", PT_FP64) else PT_FP32
+    _check(load_library().pt_energy_noalloc(d_spins, precision, int(L), int(n_configs), d_couplings,
+                                            d_energy, stream))
 
 
 def pt_get_stats(h, proposals=None, accepts=None, round_trips=None, perm=None):
