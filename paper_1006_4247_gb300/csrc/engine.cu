@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -397,6 +398,28 @@ pt_status create_impl(pt_handle* out, int n_samples, const int* Ls, const int* N
     d.n_q = e->sumNT;
     d.max_NT = 0;
     for (int v : e->NT) d.max_NT = std::max(d.max_NT, v);
+    d.min_half = 1 << 30;
+    for (const SampleDesc& sd : e->samples) d.min_half = std::min(d.min_half, sd.half);
+    {
+        int dev = 0, nsm = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+            d.n_sm = nsm;
+        else
+            d.n_sm = 1;
+        // PT_EXCHANGE_CLUSTER = 1, 2, 4 or 8 fixes the CTAs per chain of the
+        // decimation and cooling/heating exchanges (default: chosen from the
+        // number of chains and SMs)
+        const char* ev = std::getenv("PT_EXCHANGE_CLUSTER");
+        const int cs = ev ? std::atoi(ev) : 0;
+        d.exchange_cluster = (cs == 1 || cs == 2 || cs == 4 || cs == 8) ? cs : 0;
+        // PT_EXCHANGE_IMPL = l2 | smem selects the exchange kernels (default:
+        // shared-memory staged where the pair fits on one SM)
+        const char* ei = std::getenv("PT_EXCHANGE_IMPL");
+        d.exchange_impl = (ei && std::strcmp(ei, "l2") == 0) ? 1 : (ei && std::strcmp(ei, "smem") == 0) ? 2 : 0;
+    }
+    d.max_half = 0;
+    for (const SampleDesc& sd : e->samples) d.max_half = std::max(d.max_half, sd.half);
 
     st = run(e, PT_KERNEL_OTHER, 1, [&]() { return launch_init_spins(d, e->fp64, e->start, e->stream); });
     if (st == PT_OK) st = compute_energy(e);

@@ -2,26 +2,40 @@
 // swap (section I, Eq. 1), the decimation swap (section III.A, Eq. aswap,
 // appendix A) and the cooling/heating swap (section III.B).
 //
-// One CTA per chain (sample, copy).  The pairs (b, b+1) are visited in
-// increasing beta, each seeing the result of the previous one, so a chain is
-// sequential in b; the lattice work of a pair (decimated sums, re-insertion,
-// cooling and heating sweeps) is spread over the CTA's threads.  The chain's
-// small state (temperature-to-buffer map, labels, energies, round-trip
-// states) is held in shared memory for the whole update.
+// The pairs (b, b+1) of a chain are visited in increasing beta, each seeing
+// the result of the previous one, so a chain is sequential in b.  The lattice
+// work of a pair (decimated sums and re-insertion, cooling and heating
+// sweeps) is spread over a thread-block cluster: every CTA of the cluster
+// owns a contiguous slice of the sites of each colour and keeps its own copy
+// of the chain's small state (temperature-to-buffer map, labels, energies,
+// round-trip states) in shared memory.  Per pair each CTA reduces its partial
+// sums, publishes them in its shared memory, and after the hardware cluster
+// barrier reads every CTA's partials through distributed shared memory and
+// adds them in rank order.  All CTAs therefore hold bit-identical sums, draw
+// the same Philox uniform and take the same decision; there is no broadcast
+// and no spin-wait.  Spins are exchanged through global memory (L2), made
+// visible across the cluster by a fence before each cluster barrier.
+#include <cooperative_groups.h>
+
 #include "kernels.h"
 #include "pt_device.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace ptk {
 
 constexpr int MAX_NT = 512;
 constexpr int EX_THREADS = 512;
+constexpr int MAX_SUMS = 4;
 
 struct ChainSmem {
     int buf[MAX_NT];
     int lab[MAX_NT];
     int rts[MAX_NT];
     double H[MAX_NT];
-    double red[32];
+    double red[MAX_SUMS * 32];
+    double slot[2][MAX_SUMS];  // published partials (double-buffered)
+    double sum[MAX_SUMS];      // cluster totals, in rank order
     int flag;
     int free0, free1;
 };
@@ -66,22 +80,42 @@ __device__ void store_chain(const DevBatch& a, const ChainDesc& cd, int NT, Chai
     if (threadIdx.x == 0) a.freebuf[ch] = make_int2(sm.free0, sm.free1);
 }
 
-// D(n) = ln I(b2 n) - ln I(b1 n) for |S| = n.  With
-// ln(sinh R / R) = R - ln(2R) + ln(1 - e^{-2R}) (appendix A) the large parts
-// reduce to (b2 - b1) n - ln(b2/b1), which keeps float accuracy; below
-// R = 1/2 the difference is taken directly.
-template <typename T>
-__device__ __forceinline__ T decim_D(T n, T b1, T b2, T db, T lr) {
-    const T R1 = b1 * n, R2 = b2 * n;
-    if (R1 >= (T)0.5)
-        return db * n - lr + M<T>::log1p_(-M<T>::exp_((T)-2 * R2)) - M<T>::log1p_(-M<T>::exp_((T)-2 * R1));
-    return ln_sinhc<T>(R2) - ln_sinhc<T>(R1);
-}
-
 __device__ __forceinline__ bool metropolis(double lnA, double u) { return lnA >= 0.0 || u < exp(lnA); }
 
+// Sum NV per-thread values over the CTA, then over the cluster in rank order;
+// the totals land in sm.sum[] of every CTA.  Global writes made before the
+// call are visible to the whole cluster after it.  `pub` counts publications
+// (uniform over the cluster) and selects the slot.
+template <typename T, int NV>
+__device__ void cluster_sum(cg::cluster_group& cl, ChainSmem& sm, const T (&v)[NV], int& pub) {
+    double tot[NV];
+    block_sum_multi<T, NV>(v, tot, sm.red);
+    const int slot = pub & 1;
+    ++pub;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < NV; ++k) sm.slot[slot][k] = tot[k];
+    __threadfence();
+    cl.sync();
+    if (threadIdx.x == 0) {
+        const int n = (int)cl.num_blocks();
+        for (int k = 0; k < NV; ++k) {
+            double s = 0.0;
+            for (int r = 0; r < n; ++r) s += cl.map_shared_rank(&sm.slot[slot][0], r)[k];
+            sm.sum[k] = s;
+        }
+    }
+    __syncthreads();
+}
+
+// Contiguous slice [lo, hi) of n items for CTA `rank` of `cs`.
+__device__ __forceinline__ void slice(int n, int rank, int cs, int& lo, int& hi) {
+    lo = (int)(((long long)n * rank) / cs);
+    hi = (int)(((long long)n * (rank + 1)) / cs);
+}
+
 // ---------------------------------------------------------------------------
-// Standard swap: Delta = (b_{i+1} - b_i)(H_{i+1} - H_i) in double.
+// Standard swap: Delta = (b_{i+1} - b_i)(H_{i+1} - H_i) in double.  No
+// lattice work: one warp per chain.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(32) k_exchange_plain(DevBatch a) {
     __shared__ ChainSmem sm;
@@ -108,6 +142,18 @@ __global__ void __launch_bounds__(32) k_exchange_plain(DevBatch a) {
     store_chain(a, cd, NT, sm, ch);
 }
 
+// D(n) = ln I(b2 n) - ln I(b1 n) for |S| = n.  With
+// ln(sinh R / R) = R - ln(2R) + ln(1 - e^{-2R}) (appendix A) the large parts
+// reduce to (b2 - b1) n - ln(b2/b1), which keeps float accuracy; below
+// R = 1/2 the difference is taken directly.
+template <typename T>
+__device__ __forceinline__ T decim_D(T n, T b1, T b2, T db, T lr) {
+    const T R1 = b1 * n, R2 = b2 * n;
+    if (R1 >= (T)0.5)
+        return db * n - lr + M<T>::log1p_(-M<T>::exp_((T)-2 * R2)) - M<T>::log1p_(-M<T>::exp_((T)-2 * R1));
+    return ln_sinhc<T>(R2) - ln_sinhc<T>(R1);
+}
+
 // ---------------------------------------------------------------------------
 // Decimation swap.  For pair i the decimated colour is d = (d0 + i) mod 2
 // (d0 from purpose 3).  ln A = sum over decimated x of
@@ -119,11 +165,16 @@ __global__ void __launch_bounds__(32) k_exchange_plain(DevBatch a) {
 template <typename T>
 __global__ void __launch_bounds__(EX_THREADS) k_exchange_decimation(DevBatch a) {
     __shared__ ChainSmem sm;
-    const int ch = blockIdx.x;
+    cg::cluster_group cl = cg::this_cluster();
+    const int cs = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+    const int ch = blockIdx.x / cs;
     const ChainDesc cd = a.chains[ch];
     const SampleDesc& sd = a.samples[cd.s];
     const int NT = sd.NT, half = sd.half;
     load_chain(a, cd, NT, sm, ch);
+    int lo, hi;
+    slice(half, rank, cs, lo, hi);
+    int pub = 0;
     const unsigned long long step = *a.d_step;
     const double* beta = a.betas + sd.beta_off;
     T* pool = (T*)a.spins + a.chain_off[ch];
@@ -139,56 +190,58 @@ __global__ void __launch_bounds__(EX_THREADS) k_exchange_decimation(DevBatch a) 
         const float* Jk = a.J + sd.J_off + (1 - d) * 3 * half;
         const T dbt = (T)(b2 - b1);
         const T lr = b1 > 0.0 ? (T)log(b2 / b1) : (T)0;
-        double lnA_part = 0.0;
-        for (int h = threadIdx.x; h < half; h += blockDim.x) {
+        T part[1] = {(T)0};
+        for (int h = lo + (int)threadIdx.x; h < hi; h += blockDim.x) {
             const Site st = site_of(sd, d, h);
             const V3<T> S1 = local_field<T>(st, half, c1 + (1 - d) * 3 * half, Jd, Jk);
             const V3<T> S2 = local_field<T>(st, half, c2 + (1 - d) * 3 * half, Jd, Jk);
             const T na = M<T>::sqrt_(dot(S1, S1)), nb = M<T>::sqrt_(dot(S2, S2));
-            const T term = decim_D<T>(na, b1t, b2t, dbt, lr) - decim_D<T>(nb, b1t, b2t, dbt, lr);
-            lnA_part += (double)term;
+            part[0] += decim_D<T>(na, b1t, b2t, dbt, lr) - decim_D<T>(nb, b1t, b2t, dbt, lr);
         }
-        const double lnA = block_sum(lnA_part, sm.red);
+        cluster_sum<T, 1>(cl, sm, part, pub);
         if (threadIdx.x == 0) {
+            const double lnA = sm.sum[0];
             const uint4 w = rng_words(a.seed, (uint32_t)cd.s, (uint32_t)i, (uint32_t)cd.copy, step, 1u);
-            a.prop[cd.pair_off + i] += 1;
             const bool ok = metropolis(lnA, u53(w.x, w.y));
             sm.flag = ok;
+            if (rank == 0) {
+                a.prop[cd.pair_off + i] += 1;
+                if (ok) a.acc[cd.pair_off + i] += 1;
+            }
             if (ok) {
-                a.acc[cd.pair_off + i] += 1;
                 int t = sm.buf[i]; sm.buf[i] = sm.buf[i + 1]; sm.buf[i + 1] = t;
                 t = sm.lab[i]; sm.lab[i] = sm.lab[i + 1]; sm.lab[i + 1] = t;
             }
         }
         __syncthreads();
         if (sm.flag) {
-            double e1 = 0.0, e2 = 0.0;
+            T e[2] = {(T)0, (T)0};
             T* n1 = pool + (long long)sm.buf[i] * (6LL * half);      // now at b1
             T* n2 = pool + (long long)sm.buf[i + 1] * (6LL * half);  // now at b2
             const uint32_t id1 = (uint32_t)(cd.copy * NT + i), id2 = id1 + 1u;
-            for (int h = threadIdx.x; h < half; h += blockDim.x) {
+            for (int h = lo + (int)threadIdx.x; h < hi; h += blockDim.x) {
                 const Site st = site_of(sd, d, h);
                 const V3<T> S1 = local_field<T>(st, half, n1 + (1 - d) * 3 * half, Jd, Jk);
                 const uint4 w1 = rng_words(a.seed, (uint32_t)cd.s, (uint32_t)st.x, id1, step, 2u);
                 const V3<T> s1 = hb_site<T>(b1t, S1, w1.x, w1.y);
                 st3(n1 + d * 3 * half, half, h, s1);
-                e1 -= (double)dot(s1, S1);
+                e[0] -= dot(s1, S1);
                 const V3<T> S2 = local_field<T>(st, half, n2 + (1 - d) * 3 * half, Jd, Jk);
                 const uint4 w2 = rng_words(a.seed, (uint32_t)cd.s, (uint32_t)st.x, id2, step, 2u);
                 const V3<T> s2 = hb_site<T>(b2t, S2, w2.x, w2.y);
                 st3(n2 + d * 3 * half, half, h, s2);
-                e2 -= (double)dot(s2, S2);
+                e[1] -= dot(s2, S2);
             }
-            const double E1 = block_sum(e1, sm.red);
-            const double E2 = block_sum(e2, sm.red);
+            cluster_sum<T, 2>(cl, sm, e, pub);
             if (threadIdx.x == 0) {
-                sm.H[i] = E1;
-                sm.H[i + 1] = E2;
+                sm.H[i] = sm.sum[0];
+                sm.H[i + 1] = sm.sum[1];
             }
+            __syncthreads();
         }
-        __syncthreads();
     }
-    store_chain(a, cd, NT, sm, ch);
+    if (rank == 0) store_chain(a, cd, NT, sm, ch);
+    cl.sync();  // no CTA leaves while others may still read its shared memory
 }
 
 // ---------------------------------------------------------------------------
@@ -205,11 +258,16 @@ __global__ void __launch_bounds__(EX_THREADS) k_exchange_decimation(DevBatch a) 
 template <typename T>
 __global__ void __launch_bounds__(EX_THREADS) k_exchange_coolheat(DevBatch a) {
     __shared__ ChainSmem sm;
-    const int ch = blockIdx.x;
+    cg::cluster_group cl = cg::this_cluster();
+    const int cs = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+    const int ch = blockIdx.x / cs;
     const ChainDesc cd = a.chains[ch];
     const SampleDesc& sd = a.samples[cd.s];
     const int NT = sd.NT, half = sd.half;
     load_chain(a, cd, NT, sm, ch);
+    int lo, hi;
+    slice(half, rank, cs, lo, hi);
+    int pub = 0;
     const unsigned long long step = *a.d_step;
     const double* beta = a.betas + sd.beta_off;
     T* pool = (T*)a.spins + a.chain_off[ch];
@@ -223,48 +281,50 @@ __global__ void __launch_bounds__(EX_THREADS) k_exchange_coolheat(DevBatch a) {
         const T* s2 = pool + (long long)sm.buf[i + 1] * rep;
         T* f1 = pool + (long long)sm.free0 * rep;
         T* f2 = pool + (long long)sm.free1 * rep;
-        double lj1 = 0.0, lj2 = 0.0, Hc = 0.0, Hh = 0.0;
+        T v[4] = {(T)0, (T)0, (T)0, (T)0};  // ln J_C(s1), ln J_C(C^-1 s2), H[C s1], H[C^-1 s2]
         // phase 1: cool colour 0 of s1 (neighbours: s1 colour 1);
         //          heat colour 1 of s2 (neighbours: s2 colour 0)
-        for (int h = threadIdx.x; h < half; h += blockDim.x) {
+        for (int h = lo + (int)threadIdx.x; h < hi; h += blockDim.x) {
             const Site st0 = site_of(sd, 0, h);
             const V3<T> S = local_field<T>(st0, half, s1 + 3 * half, J0, J1);
             V3<T> s = ld3(s1, half, h);
-            lj1 += (double)cool_site<T>(eps, S, s);
+            v[0] += cool_site<T>(eps, S, s);
             st3(f1, half, h, s);
             const Site st1 = site_of(sd, 1, h);
             const V3<T> S2 = local_field<T>(st1, half, s2, J1, J0);
             V3<T> u = ld3(s2 + 3 * half, half, h);
-            lj2 += (double)heat_site<T>(eps, S2, u);
+            v[1] += heat_site<T>(eps, S2, u);
             st3(f2 + 3 * half, half, h, u);
         }
-        __syncthreads();
+        __threadfence();
+        cl.sync();
         // phase 2: cool colour 1 of s1 (neighbours: cooled colour 0 in f1);
         //          heat colour 0 of s2 (neighbours: heated colour 1 in f2)
-        for (int h = threadIdx.x; h < half; h += blockDim.x) {
+        for (int h = lo + (int)threadIdx.x; h < hi; h += blockDim.x) {
             const Site st1 = site_of(sd, 1, h);
             const V3<T> S = local_field<T>(st1, half, f1, J1, J0);
             V3<T> s = ld3(s1 + 3 * half, half, h);
-            lj1 += (double)cool_site<T>(eps, S, s);
+            v[0] += cool_site<T>(eps, S, s);
             st3(f1 + 3 * half, half, h, s);
-            Hc -= (double)dot(s, S);
+            v[2] -= dot(s, S);
             const Site st0 = site_of(sd, 0, h);
             const V3<T> S2 = local_field<T>(st0, half, f2 + 3 * half, J0, J1);
             V3<T> u = ld3(s2, half, h);
-            lj2 += (double)heat_site<T>(eps, S2, u);
+            v[1] += heat_site<T>(eps, S2, u);
             st3(f2, half, h, u);
-            Hh -= (double)dot(u, S2);
+            v[3] -= dot(u, S2);
         }
-        const double LJ1 = block_sum(lj1, sm.red);
-        const double LJ2 = block_sum(lj2, sm.red);
-        const double HC = block_sum(Hc, sm.red);
-        const double HH = block_sum(Hh, sm.red);
+        cluster_sum<T, 4>(cl, sm, v, pub);
         if (threadIdx.x == 0) {
+            const double LJ1 = sm.sum[0], LJ2 = sm.sum[1], HC = sm.sum[2], HH = sm.sum[3];
             const double lnA = -b2 * HC - b1 * HH + b1 * sm.H[i] + b2 * sm.H[i + 1] + LJ1 - LJ2;
             const uint4 w = rng_words(a.seed, (uint32_t)cd.s, (uint32_t)i, (uint32_t)cd.copy, step, 1u);
-            a.prop[cd.pair_off + i] += 1;
-            if (metropolis(lnA, u53(w.x, w.y))) {
-                a.acc[cd.pair_off + i] += 1;
+            const bool ok = metropolis(lnA, u53(w.x, w.y));
+            if (rank == 0) {
+                a.prop[cd.pair_off + i] += 1;
+                if (ok) a.acc[cd.pair_off + i] += 1;
+            }
+            if (ok) {
                 const int o1 = sm.buf[i], o2 = sm.buf[i + 1];
                 sm.buf[i] = sm.free1;      // C^-1(s2) at b1
                 sm.buf[i + 1] = sm.free0;  // C(s1) at b2
@@ -277,19 +337,51 @@ __global__ void __launch_bounds__(EX_THREADS) k_exchange_coolheat(DevBatch a) {
         }
         __syncthreads();
     }
-    store_chain(a, cd, NT, sm, ch);
+    if (rank == 0) store_chain(a, cd, NT, sm, ch);
+    cl.sync();  // no CTA leaves while others may still read its shared memory
+}
+
+// Cluster size per chain: enough CTAs to cover the SMs at least once, a
+// power of two <= 8, and at least 64 sites of each colour per CTA.
+static int cluster_size(const DevBatch& b) {
+    int cs = 1;
+    while (cs < 8 && b.n_chains * cs < b.n_sm && b.min_half / (2 * cs) >= 64) cs *= 2;
+    return cs;
+}
+
+template <typename K>
+static cudaError_t launch_cluster(K kernel, const DevBatch& b, int cs, cudaStream_t st) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(b.n_chains * cs);
+    cfg.blockDim = dim3(EX_THREADS);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, b);
 }
 
 cudaError_t launch_exchange(const DevBatch& b, bool fp64, int mode, cudaStream_t st) {
     if (mode == 0) {
         k_exchange_plain<<<b.n_chains, 32, 0, st>>>(b);
-    } else if (mode == 1) {
-        if (fp64) k_exchange_decimation<double><<<b.n_chains, EX_THREADS, 0, st>>>(b);
-        else k_exchange_decimation<float><<<b.n_chains, EX_THREADS, 0, st>>>(b);
-    } else {
-        if (fp64) k_exchange_coolheat<double><<<b.n_chains, EX_THREADS, 0, st>>>(b);
-        else k_exchange_coolheat<float><<<b.n_chains, EX_THREADS, 0, st>>>(b);
+        return cudaGetLastError();
     }
+    if (b.exchange_impl != 1 && exchange_smem_supported(mode, b.max_half, fp64))
+        return launch_exchange_smem(b, fp64, mode, b.max_half, st);
+    const int cs = b.exchange_cluster > 0 ? b.exchange_cluster : cluster_size(b);
+    cudaError_t e;
+    if (mode == 1)
+        e = fp64 ? launch_cluster(k_exchange_decimation<double>, b, cs, st)
+                 : launch_cluster(k_exchange_decimation<float>, b, cs, st);
+    else
+        e = fp64 ? launch_cluster(k_exchange_coolheat<double>, b, cs, st)
+                 : launch_cluster(k_exchange_coolheat<float>, b, cs, st);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

@@ -1,0 +1,326 @@
+// exchange_smem.cu -- decimation and cooling/heating exchanges (sections
+// III.A and III.B of Hasenbusch & Schaefer) with the configurations of the
+// current pair staged in shared memory, for lattices whose configurations fit
+// on one SM (float: L <= 16).
+//
+// One CTA per chain walks the pairs (b, b+1) in increasing beta.  The
+// configuration that sits at beta_{i+1} after pair i is the first
+// configuration of pair i+1, so it stays on chip: per pair one configuration
+// is read from global memory and at most one is written back (the one whose
+// temperature is final).  Neighbour gathers of the cooling and heating sweeps,
+// the decimated sums and the re-insertion heat bath all read shared memory.
+// Global buffers keep their identities: a transformed configuration is written
+// into the buffer of the configuration it replaces, and the
+// temperature-to-buffer map records where each configuration lives.
+#include "kernels.h"
+#include "pt_device.cuh"
+
+namespace ptk {
+
+constexpr int SX_THREADS = 1024;
+constexpr int SX_MAX_NT = 512;
+
+struct SxSmem {
+    int buf[SX_MAX_NT];
+    int lab[SX_MAX_NT];
+    int rts[SX_MAX_NT];
+    double H[SX_MAX_NT];
+    double red[4 * 32];
+    int flag;
+};
+
+__device__ void sx_load_state(const DevBatch& a, const ChainDesc& cd, int NT, SxSmem& sm) {
+    for (int b = threadIdx.x; b < NT; b += blockDim.x) {
+        sm.buf[b] = a.bufmap[cd.r0 + b];
+        sm.lab[b] = a.label[cd.r0 + b];
+        sm.rts[b] = a.rt_state[cd.r0 + b];
+        sm.H[b] = a.H[cd.r0 + b];
+    }
+    __syncthreads();
+}
+
+__device__ void sx_store_state(const DevBatch& a, const ChainDesc& cd, int NT, SxSmem& sm, int ch) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int top = sm.lab[0], bot = sm.lab[NT - 1];
+        if (sm.rts[bot] == 1) sm.rts[bot] = 2;
+        if (sm.rts[top] == 2) {
+            a.rt_count[ch] += 1;
+            sm.rts[top] = 1;
+        } else if (sm.rts[top] == 0) {
+            sm.rts[top] = 1;
+        }
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < NT; b += blockDim.x) {
+        a.bufmap[cd.r0 + b] = sm.buf[b];
+        a.label[cd.r0 + b] = sm.lab[b];
+        a.rt_state[cd.r0 + b] = sm.rts[b];
+        a.H[cd.r0 + b] = sm.H[b];
+    }
+}
+
+// Copy n elements (a multiple of the 16-byte vector width) between global and
+// shared memory with the whole CTA.
+template <typename T>
+__device__ __forceinline__ void sx_copy(T* __restrict__ dst, const T* __restrict__ src, int n) {
+    constexpr int VW = 16 / sizeof(T);
+    for (int q = threadIdx.x * VW; q < n; q += blockDim.x * VW) {
+        T v[VW];
+        ldv<T, VW>(src + q, v);
+        stv<T, VW>(dst + q, v);
+    }
+}
+
+__device__ __forceinline__ bool sx_metropolis(double lnA, double u) { return lnA >= 0.0 || u < exp(lnA); }
+
+template <typename T>
+__device__ __forceinline__ T sx_decim_D(T n, T b1, T b2, T db, T lr) {
+    const T R1 = b1 * n, R2 = b2 * n;
+    if (R1 >= (T)0.5)
+        return db * n - lr + M<T>::log1p_(-M<T>::exp_((T)-2 * R2)) - M<T>::log1p_(-M<T>::exp_((T)-2 * R1));
+    return ln_sinhc<T>(R2) - ln_sinhc<T>(R1);
+}
+
+// ---------------------------------------------------------------------------
+// Cooling/heating: slots hold s1 (now at beta_i), s2 (at beta_{i+1}) and the
+// transforms f1 = C(s1), f2 = C^-1(s2).  Accept: f2 is final at beta_i and is
+// written into s1's buffer; f1 moves on as the next s1 and will be written
+// into s2's buffer.  Reject: s1 is final (written back if it was transformed
+// earlier in this update); s2 moves on.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(SX_THREADS, 1) k_exchange_coolheat_smem(DevBatch a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ SxSmem sm;
+    const int ch = blockIdx.x;
+    const ChainDesc cd = a.chains[ch];
+    const SampleDesc& sd = a.samples[cd.s];
+    const int NT = sd.NT, half = sd.half, n3 = 6 * half;
+    T* const slots = reinterpret_cast<T*>(smem_raw);
+    auto slot = [&](int q) { return slots + (size_t)q * n3; };
+    sx_load_state(a, cd, NT, sm);
+    T* pool = (T*)a.spins + a.chain_off[ch];
+    const float* J0 = a.J + sd.J_off;
+    const float* J1 = a.J + sd.J_off + 3 * half;
+    const unsigned long long step = *a.d_step;
+    const double* beta = a.betas + sd.beta_off;
+    int A = 0;                      // slot of s1
+    int ownerA = sm.buf[0];         // global buffer of s1
+    bool dirtyA = false;
+    sx_copy(slot(A), pool + (long long)ownerA * n3, n3);
+    for (int i = 0; i + 1 < NT; ++i) {
+        const int B = (A + 1) & 3, F1 = (A + 2) & 3, F2 = (A + 3) & 3;
+        const int ownerB = sm.buf[i + 1];
+        sx_copy(slot(B), pool + (long long)ownerB * n3, n3);
+        __syncthreads();
+        const T eps = (T)a.eps[sd.eps_off + i];
+        const T* s1 = slot(A);
+        const T* s2 = slot(B);
+        T* f1 = slot(F1);
+        T* f2 = slot(F2);
+        T lj1 = (T)0, lj2 = (T)0, hc = (T)0, hh = (T)0;  // per-thread partials of a few sites
+        for (int h = threadIdx.x; h < half; h += blockDim.x) {
+            const Site st0 = site_of(sd, 0, h);
+            const V3<T> S = local_field<T>(st0, half, s1 + 3 * half, J0, J1);
+            V3<T> s = ld3(s1, half, h);
+            lj1 += cool_site<T>(eps, S, s);
+            st3(f1, half, h, s);
+            const Site st1 = site_of(sd, 1, h);
+            const V3<T> S2 = local_field<T>(st1, half, s2, J1, J0);
+            V3<T> u = ld3(s2 + 3 * half, half, h);
+            lj2 += heat_site<T>(eps, S2, u);
+            st3(f2 + 3 * half, half, h, u);
+        }
+        __syncthreads();
+        for (int h = threadIdx.x; h < half; h += blockDim.x) {
+            const Site st1 = site_of(sd, 1, h);
+            const V3<T> S = local_field<T>(st1, half, f1, J1, J0);
+            V3<T> s = ld3(s1 + 3 * half, half, h);
+            lj1 += cool_site<T>(eps, S, s);
+            st3(f1 + 3 * half, half, h, s);
+            hc -= dot(s, S);
+            const Site st0 = site_of(sd, 0, h);
+            const V3<T> S2 = local_field<T>(st0, half, f2 + 3 * half, J0, J1);
+            V3<T> u = ld3(s2, half, h);
+            lj2 += heat_site<T>(eps, S2, u);
+            st3(f2, half, h, u);
+            hh -= dot(u, S2);
+        }
+        const T part[4] = {lj1, lj2, hc, hh};
+        double tot[4];
+        block_sum_multi<T, 4>(part, tot, sm.red);
+        const double LJ1 = tot[0], LJ2 = tot[1], HC = tot[2], HH = tot[3];
+        if (threadIdx.x == 0) {
+            const double b1 = beta[i], b2 = beta[i + 1];
+            const double lnA = -b2 * HC - b1 * HH + b1 * sm.H[i] + b2 * sm.H[i + 1] + LJ1 - LJ2;
+            const uint4 w = rng_words(a.seed, (uint32_t)cd.s, (uint32_t)i, (uint32_t)cd.copy, step, 1u);
+            const bool ok = sx_metropolis(lnA, u53(w.x, w.y));
+            a.prop[cd.pair_off + i] += 1;
+            sm.flag = ok;
+            if (ok) {
+                a.acc[cd.pair_off + i] += 1;
+                sm.buf[i] = ownerA;       // C^-1(s2) goes into s1's old buffer
+                sm.buf[i + 1] = ownerB;   // C(s1) will go into s2's old buffer
+                sm.H[i] = HH;
+                sm.H[i + 1] = HC;
+                const int t = sm.lab[i]; sm.lab[i] = sm.lab[i + 1]; sm.lab[i + 1] = t;
+            }
+        }
+        __syncthreads();
+        if (sm.flag) {
+            sx_copy(pool + (long long)ownerA * n3, f2, n3);
+            A = F1;
+            ownerA = ownerB;
+            dirtyA = true;
+        } else {
+            if (dirtyA) sx_copy(pool + (long long)ownerA * n3, slot(A), n3);
+            A = B;
+            ownerA = ownerB;
+            dirtyA = false;
+        }
+        __syncthreads();
+    }
+    if (dirtyA) sx_copy(pool + (long long)ownerA * n3, slot(A), n3);
+    sx_store_state(a, cd, NT, sm, ch);
+}
+
+// ---------------------------------------------------------------------------
+// Decimation: slots hold s1 (at beta_i) and s2 (at beta_{i+1}).  Accept: the
+// kept colours change temperature, the decimated colour of both is redrawn
+// at the new beta; s2 is then final at beta_i (written back), s1 moves on to
+// beta_{i+1}.  Reject: s1 is final (written back if re-inserted earlier), s2
+// moves on.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(SX_THREADS, 1) k_exchange_decimation_smem(DevBatch a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ SxSmem sm;
+    const int ch = blockIdx.x;
+    const ChainDesc cd = a.chains[ch];
+    const SampleDesc& sd = a.samples[cd.s];
+    const int NT = sd.NT, half = sd.half, n3 = 6 * half;
+    T* const slots = reinterpret_cast<T*>(smem_raw);
+    auto slot = [&](int q) { return slots + (size_t)q * n3; };
+    sx_load_state(a, cd, NT, sm);
+    T* pool = (T*)a.spins + a.chain_off[ch];
+    const unsigned long long step = *a.d_step;
+    const double* beta = a.betas + sd.beta_off;
+    const uint4 wd = rng_words(a.seed, (uint32_t)cd.s, 0u, (uint32_t)cd.copy, step, 3u);
+    const int d0 = (int)(wd.x & 1u);
+    int A = 0;
+    int ownerA = sm.buf[0];
+    bool dirtyA = false;
+    sx_copy(slot(A), pool + (long long)ownerA * n3, n3);
+    for (int i = 0; i + 1 < NT; ++i) {
+        const int B = 1 - A;
+        const int ownerB = sm.buf[i + 1];
+        sx_copy(slot(B), pool + (long long)ownerB * n3, n3);
+        __syncthreads();
+        const int d = (d0 + i) & 1;
+        const double b1 = beta[i], b2 = beta[i + 1];
+        const T b1t = (T)b1, b2t = (T)b2, dbt = (T)(b2 - b1);
+        const T lr = b1 > 0.0 ? (T)log(b2 / b1) : (T)0;
+        const float* Jd = a.J + sd.J_off + d * 3 * half;
+        const float* Jk = a.J + sd.J_off + (1 - d) * 3 * half;
+        T* c1 = slot(A);
+        T* c2 = slot(B);
+        T part[1] = {(T)0};
+        for (int h = threadIdx.x; h < half; h += blockDim.x) {
+            const Site st = site_of(sd, d, h);
+            const V3<T> S1 = local_field<T>(st, half, c1 + (1 - d) * 3 * half, Jd, Jk);
+            const V3<T> S2 = local_field<T>(st, half, c2 + (1 - d) * 3 * half, Jd, Jk);
+            const T na = M<T>::sqrt_(dot(S1, S1)), nb = M<T>::sqrt_(dot(S2, S2));
+            part[0] += sx_decim_D<T>(na, b1t, b2t, dbt, lr) - sx_decim_D<T>(nb, b1t, b2t, dbt, lr);
+        }
+        double tot1[1];
+        block_sum_multi<T, 1>(part, tot1, sm.red);
+        const double lnA = tot1[0];
+        if (threadIdx.x == 0) {
+            const uint4 w = rng_words(a.seed, (uint32_t)cd.s, (uint32_t)i, (uint32_t)cd.copy, step, 1u);
+            const bool ok = sx_metropolis(lnA, u53(w.x, w.y));
+            a.prop[cd.pair_off + i] += 1;
+            sm.flag = ok;
+            if (ok) {
+                a.acc[cd.pair_off + i] += 1;
+                sm.buf[i] = ownerB;
+                sm.buf[i + 1] = ownerA;
+                const int t = sm.lab[i]; sm.lab[i] = sm.lab[i + 1]; sm.lab[i + 1] = t;
+            }
+        }
+        __syncthreads();
+        if (sm.flag) {
+            // c2 now at b1 (replica id of index i), c1 at b2 (index i+1)
+            T e12[2] = {(T)0, (T)0};
+            const uint32_t id1 = (uint32_t)(cd.copy * NT + i), id2 = id1 + 1u;
+            for (int h = threadIdx.x; h < half; h += blockDim.x) {
+                const Site st = site_of(sd, d, h);
+                const V3<T> Sa = local_field<T>(st, half, c2 + (1 - d) * 3 * half, Jd, Jk);
+                const uint4 w1 = rng_words(a.seed, (uint32_t)cd.s, (uint32_t)st.x, id1, step, 2u);
+                const V3<T> sa = hb_site<T>(b1t, Sa, w1.x, w1.y);
+                st3(c2 + d * 3 * half, half, h, sa);
+                e12[0] -= dot(sa, Sa);
+                const V3<T> Sb = local_field<T>(st, half, c1 + (1 - d) * 3 * half, Jd, Jk);
+                const uint4 w2 = rng_words(a.seed, (uint32_t)cd.s, (uint32_t)st.x, id2, step, 2u);
+                const V3<T> sb = hb_site<T>(b2t, Sb, w2.x, w2.y);
+                st3(c1 + d * 3 * half, half, h, sb);
+                e12[1] -= dot(sb, Sb);
+            }
+            double E[2];
+            block_sum_multi<T, 2>(e12, E, sm.red);
+            if (threadIdx.x == 0) {
+                sm.H[i] = E[0];
+                sm.H[i + 1] = E[1];
+            }
+            __syncthreads();
+            sx_copy(pool + (long long)ownerB * n3, c2, n3);  // final at b1
+            // c1 stays in slot A, now at b2, owned by its own buffer, modified
+            dirtyA = true;
+        } else {
+            if (dirtyA) sx_copy(pool + (long long)ownerA * n3, c1, n3);
+            A = B;
+            ownerA = ownerB;
+            dirtyA = false;
+        }
+        __syncthreads();
+    }
+    if (dirtyA) sx_copy(pool + (long long)ownerA * n3, slot(A), n3);
+    sx_store_state(a, cd, NT, sm, ch);
+}
+
+size_t exchange_smem_bytes(int mode, int half, bool fp64) {
+    return (size_t)(mode == 2 ? 4 : 2) * 6 * half * (fp64 ? 8 : 4);
+}
+
+bool exchange_smem_supported(int mode, int max_half, bool fp64) {
+    return (mode == 1 || mode == 2) && exchange_smem_bytes(mode, max_half, fp64) <= 200 * 1024;
+}
+
+cudaError_t launch_exchange_smem(const DevBatch& b, bool fp64, int mode, int max_half, cudaStream_t st) {
+    const size_t smem = exchange_smem_bytes(mode, max_half, fp64);
+    cudaError_t e;
+    if (mode == 2) {
+        if (fp64) {
+            e = cudaFuncSetAttribute(k_exchange_coolheat_smem<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            k_exchange_coolheat_smem<double><<<b.n_chains, SX_THREADS, smem, st>>>(b);
+        } else {
+            e = cudaFuncSetAttribute(k_exchange_coolheat_smem<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            k_exchange_coolheat_smem<float><<<b.n_chains, SX_THREADS, smem, st>>>(b);
+        }
+    } else {
+        if (fp64) {
+            e = cudaFuncSetAttribute(k_exchange_decimation_smem<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            k_exchange_decimation_smem<double><<<b.n_chains, SX_THREADS, smem, st>>>(b);
+        } else {
+            e = cudaFuncSetAttribute(k_exchange_decimation_smem<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            k_exchange_decimation_smem<float><<<b.n_chains, SX_THREADS, smem, st>>>(b);
+        }
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace ptk

@@ -34,6 +34,11 @@ struct DevBatch {
     double* chi;                    // [sum NT]
     int n_samples, n_chains, n_reps, n_tiles, n_q;
     int max_NT;
+    int min_half;                   // smallest L^3/2 of the batch
+    int n_sm;                       // multiprocessors of the device
+    int exchange_cluster;           // CTAs per chain in the exchange (0: automatic)
+    int exchange_impl;              // 0 automatic, 1 global-memory clusters, 2 shared-memory staged
+    int max_half;                   // largest L^3/2 of the batch
     // half-sweep tiles are grouped by vector width (sites per thread)
     int vclass_begin[3], vclass_count[3], vclass_width[3];
 };
@@ -54,6 +59,11 @@ cudaError_t launch_init_spins(const DevBatch& b, bool fp64, int ordered, cudaStr
 cudaError_t launch_advance_step(const DevBatch& b, int by, cudaStream_t st);
 cudaError_t launch_overlap(const DevBatch& b, bool fp64, cudaStream_t st);
 cudaError_t launch_exchange(const DevBatch& b, bool fp64, int mode, cudaStream_t st);
+
+// Decimation / cooling-heating exchanges with the pair staged in shared
+// memory (one CTA per chain), for configurations that fit on one SM.
+bool exchange_smem_supported(int mode, int max_half, bool fp64);
+cudaError_t launch_exchange_smem(const DevBatch& b, bool fp64, int mode, int max_half, cudaStream_t st);
 
 // Resident sweep blocks: one CTA per replica runs n_hb + n_or sweeps in shared
 // memory and writes H[r].

@@ -128,6 +128,23 @@ template <> struct M<double> {
     static constexpr double pi = CUDART_PI;
 };
 
+// Math of the cooling / heating transforms.  In float the hardware
+// approximations are used for sin, cos and log (arguments stay in [-pi, pi],
+// absolute error ~2^-21); the double path keeps the accurate library calls.
+template <typename T> struct MX;
+template <> struct MX<float> {
+    static __device__ __forceinline__ void sincos_(float x, float* s, float* c) { __sincosf(x, s, c); }
+    static __device__ __forceinline__ float sin_(float x) { return __sinf(x); }
+    static __device__ __forceinline__ float cos_(float x) { return __cosf(x); }
+    static __device__ __forceinline__ float log_(float x) { return __logf(x); }
+};
+template <> struct MX<double> {
+    static __device__ __forceinline__ void sincos_(double x, double* s, double* c) { sincos(x, s, c); }
+    static __device__ __forceinline__ double sin_(double x) { return sin(x); }
+    static __device__ __forceinline__ double cos_(double x) { return cos(x); }
+    static __device__ __forceinline__ double log_(double x) { return log(x); }
+};
+
 template <typename T> struct V3 { T x, y, z; };
 
 template <typename T>
@@ -229,11 +246,15 @@ __device__ __forceinline__ V3<T> hb_site(T beta, const V3<T>& S, uint32_t w0, ui
 }
 
 // Overrelaxation (section III.C): reflection of s about S; S = 0 keeps s.
+// In float the quotient uses the hardware reciprocal (2 ulp).
+__device__ __forceinline__ float or_quot(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double or_quot(double a, double b) { return a / b; }
+
 template <typename T>
 __device__ __forceinline__ void or_site(const V3<T>& S, V3<T>& s) {
     const T SS = dot(S, S);
     if (SS > (T)0) {
-        const T f = (T)2 * dot(s, S) / SS;
+        const T f = or_quot((T)2 * dot(s, S), SS);
         s.x = f * S.x - s.x;
         s.y = f * S.y - s.y;
         s.z = f * S.z - s.z;
@@ -254,7 +275,7 @@ __device__ __forceinline__ T ln_sinhc(T R) {
 }
 
 template <typename T>
-__device__ __forceinline__ T sinc_(T a) { return a == (T)0 ? (T)1 : M<T>::sin_(a) / a; }
+__device__ __forceinline__ T sinc_(T a) { return a == (T)0 ? (T)1 : MX<T>::sin_(a) / a; }
 
 // Cooling step (section III.B): rotate s towards S by alpha = eps |p|,
 // p = S - (S.s) s; returns ln det J_f = ln[(1 - eps S.s)(cos a - eps S.s sinc a)].
@@ -264,21 +285,25 @@ __device__ __forceinline__ T cool_site(T eps, const V3<T>& S, V3<T>& s) {
     const V3<T> p = {S.x - sS * s.x, S.y - sS * s.y, S.z - sS * s.z};
     const T pn = M<T>::sqrt_(dot(p, p));
     const T alpha = eps * pn;
-    const T ca = M<T>::cos_(alpha), sc = sinc_(alpha);
+    const T ca = MX<T>::cos_(alpha), sc = sinc_(alpha);
     const T j = ((T)1 - eps * sS) * (ca - eps * sS * sc);
     const T f = eps * sc;
     s.x = s.x * ca + p.x * f;
     s.y = s.y * ca + p.y * f;
     s.z = s.z * ca + p.z * f;
     renorm(s);
-    return M<T>::log_(fabs(j));
+    return MX<T>::log_(fabs(j));
 }
 
-// Heating step = inverse cooling step: theta' given, solve
-// theta - e sin(theta) = theta' (e = eps |S| < 1) by Newton iterations from
-// theta' + e sin(theta') until the step is below the precision's tolerance
-// (at most newton_max), rotate s' away from S by theta - theta'.  Returns
-// ln det J_f at the pre-image.
+// Heating step = inverse cooling step: theta' (angle between s' and S) given,
+// find theta with theta - e sin(theta) = theta', e = eps |S| < 1, and rotate
+// s' away from S by alpha = theta - theta'.  The unknown is taken to be alpha
+// itself: alpha = e sin(theta' + alpha), solved by Newton's method from
+// alpha = e sin(theta') with cos(theta') = s'.S/|S| and sin(theta') = |p|/|S|
+// read off the geometry, so no angle is ever formed.  At the solution
+// alpha = e sin(theta), hence the Jacobian factors and the rotation reuse
+// sin(alpha), cos(alpha).  Returns ln det J_f at the pre-image,
+// ln[(1 - e cos(theta))(cos(alpha) - e cos(theta) sin(alpha)/alpha)].
 template <typename T>
 __device__ __forceinline__ T heat_site(T eps, const V3<T>& S, V3<T>& s) {
     const T nS = M<T>::sqrt_(dot(S, S));
@@ -286,31 +311,30 @@ __device__ __forceinline__ T heat_site(T eps, const V3<T>& S, V3<T>& s) {
     const V3<T> p = {S.x - sS * s.x, S.y - sS * s.y, S.z - sS * s.z};
     const T pn = M<T>::sqrt_(dot(p, p));
     const T e = eps * nS;
-    const T thp = M<T>::atan2_(pn, sS);
-    T th = thp + e * M<T>::sin_(thp);
+    const T inv = nS > (T)0 ? (T)1 / nS : (T)0;
+    const T cp = nS > (T)0 ? sS * inv : (T)1;  // cos(theta')
+    const T sp = pn * inv;                     // sin(theta')
+    T alpha = e * sp, sa, ca;
+    MX<T>::sincos_(alpha, &sa, &ca);
     for (int it = 0; it < M<T>::newton_max; ++it) {
-        T sn, cs;
-        M<T>::sincos_(th, &sn, &cs);
-        const T d = (th - e * sn - thp) / ((T)1 - e * cs);
-        th -= d;
-        th = th < (T)0 ? (T)0 : (th > M<T>::pi ? M<T>::pi : th);
+        // f = alpha - e sin(theta' + alpha), f' = 1 - e cos(theta' + alpha)
+        const T sth = sp * ca + cp * sa, cth = cp * ca - sp * sa;
+        const T d = (alpha - e * sth) / ((T)1 - e * cth);
+        alpha -= d;
+        MX<T>::sincos_(alpha, &sa, &ca);
         if (fabs(d) < M<T>::newton_tol) break;
     }
-    const T alpha = th - thp;
     if (pn > (T)0) {
-        T sa, ca;
-        M<T>::sincos_(alpha, &sa, &ca);
         const T f = sa / pn;
         s.x = s.x * ca - p.x * f;
         s.y = s.y * ca - p.y * f;
         s.z = s.z * ca - p.z * f;
         renorm(s);
     }
-    T sth, cth;
-    M<T>::sincos_(th, &sth, &cth);
-    const T al = e * sth;
-    const T j = ((T)1 - e * cth) * (M<T>::cos_(al) - e * cth * sinc_(al));
-    return M<T>::log_(fabs(j));
+    const T cth = cp * ca - sp * sa;  // cos(theta)
+    const T sinc = alpha == (T)0 ? (T)1 : sa / alpha;
+    const T j = ((T)1 - e * cth) * (ca - e * cth * sinc);
+    return MX<T>::log_(fabs(j));
 }
 
 // ---------------------------------------------------------------------------
@@ -347,6 +371,59 @@ __device__ __forceinline__ void stv(T* __restrict__ p, const T (&o)[V]) {
 }
 
 // ---------------------------------------------------------------------------
+// Neighbour field of V consecutive sites h0 .. h0+V-1 of one row (Eq. bigS),
+// direction by direction: for each of the six directions the coupling vector
+// and the three component vectors of the neighbours are loaded, accumulated
+// into S and dropped, so few registers stay live.  `oth` is the other
+// colour's [comp][half] array, Jown / Joth the forward couplings of the two
+// colours; p is the row's checkerboard offset, xs the index of the +-x
+// neighbour that wraps around the row, hy*/hz* the rows' first indices.
+// ---------------------------------------------------------------------------
+template <typename T, int V>
+__device__ __forceinline__ void nbr_field(const T* __restrict__ oth, const float* __restrict__ Jown,
+                                          const float* __restrict__ Joth, int half, int h0, int xs,
+                                          int hyp, int hym, int hzp, int hzm, int p, T (&S)[3][V]) {
+    {   // +-x: the same row of the other colour, shifted by one (plus xs)
+        float jp[V], jm[V];
+        ldv_nc<float, V>(Jown + h0, jp);
+        {
+            float jx[V];
+            ldv_nc<float, V>(Joth + h0, jx);
+            const float jxs = __ldg(Joth + xs);
+#pragma unroll
+            for (int v = 0; v < V; ++v) jm[v] = p ? jx[v] : (v == 0 ? jxs : jx[v - 1]);
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const T* o = oth + c * half;
+            T O[V];
+            ldv<T, V>(o + h0, O);
+            const T os = o[xs];
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const T xp = p ? (v == V - 1 ? os : O[v + 1]) : O[v];
+                const T xm = p ? O[v] : (v == 0 ? os : O[v - 1]);
+                S[c][v] = (T)jp[v] * xp + (T)jm[v] * xm;
+            }
+        }
+    }
+    const float* jsrc[4] = {Jown + half + h0, Joth + half + hym, Jown + 2 * half + h0, Joth + 2 * half + hzm};
+    const int nrow[4] = {hyp, hym, hzp, hzm};
+#pragma unroll
+    for (int dir = 0; dir < 4; ++dir) {
+        float jd[V];
+        ldv_nc<float, V>(jsrc[dir], jd);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            T n[V];
+            ldv<T, V>(oth + c * half + nrow[dir], n);
+#pragma unroll
+            for (int v = 0; v < V; ++v) S[c][v] += (T)jd[v] * n[v];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Deterministic block reduction of a double (blockDim.x multiple of 32,
 // <= 1024).  All threads must call it; the result is valid in thread 0.
 // ---------------------------------------------------------------------------
@@ -354,6 +431,33 @@ __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
     return v;
+}
+
+// Sum of NV values over the CTA, for values that each thread accumulated in
+// T over its few sites: the 32 lanes of a warp are added in T, the warp sums
+// in double (so float work stays on the float pipes and at most 32 float
+// terms meet before the sum is carried in double).  One pass, two barriers;
+// results valid in thread 0.  sh must hold NV * 32 doubles.
+template <typename T, int NV>
+__device__ __forceinline__ void block_sum_multi(const T (&v)[NV], double (&out)[NV], double* sh) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        T x = v[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xFFFFFFFFu, x, o);
+        if (lane == 0) sh[k * 32 + wid] = (double)x;
+    }
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    if (wid == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double r = (lane < nw) ? sh[k * 32 + lane] : 0.0;
+            out[k] = warp_sum(r);
+        }
+    }
 }
 
 __device__ __forceinline__ double block_sum(double v, double* sh /* >= 32 doubles */) {

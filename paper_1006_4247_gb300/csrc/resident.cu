@@ -45,39 +45,9 @@ __device__ __forceinline__ double res_halfsweep(T* __restrict__ sm, const float*
         const int hyp = ih0 + hL * (jp + L * k), hym = ih0 + hL * (jm + L * k);
         const int hzp = ih0 + hL * (j + L * kp), hzm = ih0 + hL * (j + L * km);
 
-        float jf[3][V], jxb[V], jyb[V], jzb[V];
-        ldv_nc<float, V>(Jown + h0, jf[0]);
-        ldv_nc<float, V>(Jown + half + h0, jf[1]);
-        ldv_nc<float, V>(Jown + 2 * half + h0, jf[2]);
-        {
-            float jx[V];
-            ldv_nc<float, V>(Joth + h0, jx);
-            const float jxs = __ldg(Joth + xs);
-#pragma unroll
-            for (int v = 0; v < V; ++v) jxb[v] = p ? jx[v] : (v == 0 ? jxs : jx[v - 1]);
-        }
-        ldv_nc<float, V>(Joth + half + hym, jyb);
-        ldv_nc<float, V>(Joth + 2 * half + hzm, jzb);
-
         T S[3][V];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const T* o = oth + c * half;
-            T O[V], Yp[V], Ym[V], Zp[V], Zm[V];
-            ldv<T, V>(o + h0, O);
-            const T os = o[xs];
-            ldv<T, V>(o + hyp, Yp);
-            ldv<T, V>(o + hym, Ym);
-            ldv<T, V>(o + hzp, Zp);
-            ldv<T, V>(o + hzm, Zm);
-#pragma unroll
-            for (int v = 0; v < V; ++v) {
-                const T xp = p ? (v == V - 1 ? os : O[v + 1]) : O[v];
-                const T xm = p ? O[v] : (v == 0 ? os : O[v - 1]);
-                S[c][v] = (T)jf[0][v] * xp + (T)jxb[v] * xm + (T)jf[1][v] * Yp[v] + (T)jyb[v] * Ym[v] +
-                          (T)jf[2][v] * Zp[v] + (T)jzb[v] * Zm[v];
-            }
-        }
+        nbr_field<T, V>(oth, Jown, Joth, half, h0, xs, hyp, hym, hzp, hzm, p, S);
+
         T s[3][V];
         if (KIND == 0) {
 #pragma unroll
