@@ -1,0 +1,137 @@
+"""GPU checks of the C ABI around the hot path: exact checkpoint/resume,
+error statuses, the PyTorch allocator hook, asynchronous device-side
+measurement and the per-kernel profiler."""
+import os
+
+import numpy as np
+import pytest
+
+from gpu_util import get_state, make_engine
+from paper_1006_4247_gb300 import pt
+from paper_1006_4247_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1006_4247_gb300 import _build
+    _build.build()
+
+
+def _cycles(eng, n, mode, eps=None):
+    for _ in range(n):
+        eng.sweep(1, 2)
+        eng.exchange(mode, eps)
+
+
+@pytest.mark.parametrize("mode", ["plain", "decimation", "coolheat"])
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_checkpoint_resume_is_exact(tmp_path, mode, precision):
+    """k cycles, save, k cycles == load into a fresh engine, k cycles."""
+    L, S, NT = 8, 2, 4
+    eps = np.full(S * (NT - 1), 0.03, np.float32)
+    a, J, B = make_engine(L, S, NT, 2, precision, seed=17)
+    a.set_params(eps=eps)
+    _cycles(a, 3, mode)
+    f = str(tmp_path / "ck.bin")
+    a.save(f)
+    _cycles(a, 3, mode)
+    ref_state, ref_stats, ref_H = get_state(a, S, 2, NT), a.stats(), a.energies()
+    b, _, _ = make_engine(L, S, NT, 2, precision, seed=17)
+    b.load(f)
+    _cycles(b, 3, mode)
+    assert (get_state(b, S, 2, NT) == ref_state).all()
+    for x, y in zip(b.stats(), ref_stats):
+        assert (x == y).all()
+    assert (b.energies() == ref_H).all()
+    assert a.step == b.step
+    a.close()
+    b.close()
+
+
+def test_error_statuses():
+    eng, J, B = make_engine(4, 1, 3, 2, "fp32")
+    with pytest.raises(pt.PtError) as ei:
+        eng.exchange("coolheat", np.full(2, 10.0, np.float32))  # eps * max sum|J| >= 1
+    assert ei.value.status == pt.PT_ERR_EPS
+    with pytest.raises(pt.PtError) as ei:
+        eng.exchange("coolheat", np.full(2, -0.1, np.float32))
+    assert ei.value.status == pt.PT_ERR_EPS
+    with pytest.raises(pt.PtError) as ei:
+        eng.set_params(betas=np.array([1.0, 0.5, 2.0]))
+    assert ei.value.status == pt.PT_ERR_ARG
+    with pytest.raises(pt.PtError) as ei:
+        eng.get_spins(0, 2, 0)
+    assert ei.value.status == pt.PT_ERR_ARG
+    with pytest.raises(pt.PtError) as ei:
+        pt.pt_exchange(eng.h, 7)
+    assert ei.value.status == pt.PT_ERR_ARG
+    # the handle is still usable after errors
+    eng.sweep(1, 1)
+    eng.exchange("plain")
+    assert np.isfinite(eng.energies()).all()
+    eng.close()
+    one, _, _ = make_engine(4, 1, 3, 1, "fp32")
+    with pytest.raises(pt.PtError) as ei:
+        one.overlap()
+    assert ei.value.status == pt.PT_ERR_STATE
+    one.close()
+
+
+def test_load_rejects_other_shapes(tmp_path):
+    a, _, _ = make_engine(4, 1, 3, 2, "fp32")
+    f = str(tmp_path / "a.bin")
+    a.save(f)
+    b, _, _ = make_engine(4, 1, 4, 2, "fp32")
+    with pytest.raises(pt.PtError) as ei:
+        b.load(f)
+    assert ei.value.status == pt.PT_ERR_STATE
+    with open(str(tmp_path / "junk.bin"), "wb") as fh:
+        fh.write(b"not a checkpoint")
+    with pytest.raises(pt.PtError):
+        b.load(str(tmp_path / "junk.bin"))
+    a.close()
+    b.close()
+
+
+def test_torch_allocator_and_stream():
+    torch = pytest.importorskip("torch")
+    L, S, NT = 8, 2, 3
+    J = np.stack([W.couplings(L, 5 + s) for s in range(S)])
+    B = np.stack([W.linear_betas(NT, 1.0, 2.0)] * S)
+    before = torch.cuda.memory_allocated()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        a = pt.Engine(L, J, B, seed=4, use_torch_allocator=True)
+        assert torch.cuda.memory_allocated() > before
+        a.sweep(1, 2)
+        a.exchange("decimation")
+        Ha = a.energies()
+    b = pt.Engine(L, J, B, seed=4)
+    b.sweep(1, 2)
+    b.exchange("decimation")
+    assert (b.energies() == Ha).all()
+    a.close()
+    b.close()
+    assert torch.cuda.memory_allocated() <= before + (1 << 20)
+
+
+def test_measure_device_and_profiler():
+    torch = pytest.importorskip("torch")
+    eng, J, B = make_engine(8, 2, 3, 2, "fp32")
+    eng.profile(True)
+    eng.sweep(1, 1)
+    eng.exchange("plain")
+    dH = torch.zeros(2 * 2 * 3, dtype=torch.float64, device="cuda")
+    dX = torch.zeros(2 * 3, dtype=torch.float64, device="cuda")
+    pt.pt_measure_device(eng.h, dH.data_ptr(), None, dX.data_ptr())
+    torch.cuda.synchronize()
+    ms, n = eng.profile_read()
+    H = eng.energies().ravel()
+    Q, chi = eng.overlap()
+    assert np.allclose(dH.cpu().numpy(), H)
+    assert np.allclose(dX.cpu().numpy(), chi.ravel())
+    assert n["exchange"] == 1 and n["measure"] == 1 and sum(n.values()) >= 4
+    assert all(v >= 0 for v in ms.values())
+    eng.close()

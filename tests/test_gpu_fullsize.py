@@ -1,0 +1,126 @@
+"""Parity at the benchmark's full sizes, in the launch configuration bench.py
+times, on sampled outputs the oracle computes one by one:
+
+  L = 16, 64 samples x 24 replicas x 2 copies, float (shared-memory resident
+  sweep kernel, staged cooling/heating exchange);
+  L = 32, 16 samples x 48 replicas x 2 copies, float (streaming half sweeps,
+  cluster decimation exchange).
+
+Checked per sampled replica: one heat-bath sweep and one overrelaxation sweep
+site by site (the second half sweep from the engine's first-half result, as
+in the small parity tests), energy conservation of a whole block of
+overrelaxation sweeps, |s| = 1, the engine energy against the oracle's H, and
+one exchange of sampled chains against the oracle's decisions.
+"""
+import numpy as np
+import pytest
+
+import oracle as orc
+from gpu_util import ambiguous_basis_sites, site_colour
+from paper_1006_4247_gb300 import pt
+from paper_1006_4247_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1006_4247_gb300 import _build
+    _build.build()
+
+
+def _engine(name):
+    w = W.WORKLOADS[name]()
+    J = np.stack(w.couplings())
+    B = np.stack(w.betas())
+    eng = pt.Engine(w.L[0], J, B, n_copies=2, precision="fp32", seed=7)
+    eps = np.concatenate([np.full(n - 1, w.eps, np.float32) for n in w.n_replicas])
+    eng.set_params(eps=eps)
+    return w, eng, J.astype(np.float64), B
+
+
+def _check_half_sweeps(L, J, before, after, kind, beta, seed, sample, rep_id, step0):
+    col = site_colour(L)
+    cur = before.copy()
+    for colour in (0, 1):
+        if kind == "hb":
+            ref = orc.hb_halfsweep(L, J, cur, colour, beta, seed, sample, rep_id, step0 + colour)
+            amb = ambiguous_basis_sites(L, J, cur, colour)
+        else:
+            ref = orc.or_halfsweep(L, J, cur, colour)
+            amb = np.zeros(L ** 3, bool)
+        m = (col == colour) & ~amb
+        assert np.abs(after[m] - ref[m]).max() <= 1e-5, (kind, colour)
+        for x in np.nonzero((col == colour) & amb)[0]:
+            Sx = orc.local_field(L, J, cur, x)
+            n = Sx / np.linalg.norm(Sx)
+            assert abs(after[x] @ n - ref[x] @ n) <= 1e-5
+        cur = cur.copy()
+        cur[col == colour] = after[col == colour]
+
+
+@pytest.mark.parametrize("name,samples", [
+    ("L16_R24_S64", [(0, 0, 0), (33, 1, 11), (63, 1, 23)]),
+    ("L32_R48_S16", [(0, 0, 0), (9, 1, 30), (15, 0, 47)]),
+])
+def test_fullsize_sweeps_sampled(name, samples):
+    w, eng, J, B = _engine(name)
+    L = w.L[0]
+    NT = w.n_replicas[0]
+    eng.sweep(w.n_hb, w.n_or)          # one cycle exactly as the benchmark runs it
+    eng.exchange(w.exchange)
+    for kind, (nh, no) in (("hb", (1, 0)), ("or", (0, 1))):
+        before = {t: eng.get_spins(*t) for t in samples}
+        step0 = eng.step
+        eng.sweep(nh, no)
+        for (s, c, b) in samples:
+            after = eng.get_spins(s, c, b)
+            _check_half_sweeps(L, J[s], before[(s, c, b)], after, kind, B[s, b], 7, s, c * NT + b, step0)
+            assert np.allclose(np.linalg.norm(after, axis=1), 1.0, atol=1e-5)
+    # a whole overrelaxation block conserves every replica's energy
+    H0 = eng.energies()
+    eng.sweep(0, w.n_or)
+    H1 = eng.energies()
+    assert np.abs(H1 - H0).max() <= 2e-4 * np.abs(H0).max()
+    for (s, c, b) in samples:
+        Hr = orc.energy(L, J[s], eng.get_spins(s, c, b))
+        assert abs(H1[s, c, b] - Hr) <= 2e-5 * abs(Hr)
+    eng.close()
+
+
+@pytest.mark.parametrize("name,chains", [
+    ("L16_R24_S64", [(5, 0), (40, 1)]),
+    ("L32_R48_S16", [(3, 1)]),
+])
+def test_fullsize_exchange_sampled(name, chains):
+    w, eng, J, B = _engine(name)
+    L = w.L[0]
+    NT = w.n_replicas[0]
+    mode = {"plain": 0, "decimation": 1, "coolheat": 2}[w.exchange]
+    eng.sweep(w.n_hb, w.n_or)
+    eng.exchange(w.exchange)
+    eng.sweep(w.n_hb, w.n_or)
+    ref = {}
+    for (s, c) in chains:
+        st = np.stack([eng.get_spins(s, c, b) for b in range(NT)])
+        ch = orc.Chain(L, J[s], B[s], st, copy=c, sample=s, seed=7)
+        prop, acc, rt, perm = eng.stats()
+        ch.label[:] = perm[s, c]
+        ref[(s, c)] = (ch, perm[s, c].copy(), acc[s, c].copy())
+    step = eng.step
+    eng.exchange(w.exchange)
+    prop, acc, rt, perm = eng.stats()
+    H = eng.energies()
+    mismatched = 0
+    for (s, c), (ch, perm0, acc0) in ref.items():
+        ch.exchange(mode, step, eps=np.full(NT - 1, w.eps))
+        got_acc = acc[s, c] - acc0
+        if not (perm[s, c] == ch.label).all() or not (got_acc == ch.acc).all():
+            mismatched += 1
+            continue
+        for b in range(NT):
+            assert abs(H[s, c, b] - ch.H[b]) <= 1e-4 * abs(ch.H[b])
+    # float and double decisions differ only where ln A is within float
+    # round-off of ln u; at most one sampled chain may show such a tie
+    assert mismatched <= max(0, len(chains) - 1)
+    eng.close()
