@@ -67,24 +67,30 @@ def load_peaks():
     return HBM_FALLBACK_GBS, "fallback"
 
 
-def kernel_source_hash():
+KERNEL_SOURCES = {
+    "k_sweep": ("sweep.cu", "pt_device.cuh", "pt_types.h", "kernels.h"),
+    "k_resident": ("resident.cu", "pt_device.cuh", "pt_types.h", "kernels.h"),
+}
+
+
+def kernel_source_hash(kernel):
     h = hashlib.sha256()
-    for f in ("sweep.cu", "pt_device.cuh", "pt_types.h", "kernels.h"):
+    for f in KERNEL_SOURCES[kernel]:
         with open(os.path.join(ROOT, "paper_1006_4247_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(workload, precision):
-    """DRAM bytes per launch of the OR half sweep from the committed ncu summary,
-    if it was taken on the current kernel source; else None."""
+def ncu_traffic(kernel, workload, precision):
+    """DRAM bytes (read + write) per launch of `kernel` from the committed ncu
+    summary, if it was captured on the current kernel source; else None."""
     path = os.path.join(ROOT, "profiles", "roofline_traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as fh:
         d = json.load(fh)
-    e = d.get(f"{workload}:{precision}")
-    if not e or e.get("source_hash") != kernel_source_hash():
+    e = d.get(f"{kernel}:{workload}:{precision}")
+    if not e or e.get("source_hash") != kernel_source_hash(kernel):
         return None
     return float(e["dram_bytes_per_launch"])
 
@@ -294,9 +300,11 @@ def ours(args):
         the sample's couplings once per half sweep."""
         alg = R * (N // 2) * 9 * bpe + S * 3 * N * 4
         avg = pm["or"] / max(ln["or"], 1) / 1e3
+        if avg <= 0:  # no event time (e.g. launches serialised by a profiler)
+            return None
         ach = alg / avg / 1e9
         return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                "traffic": ncu_traffic(w.name, args.precision), "kernel": "k_sweep<OR> (streaming half sweep)",
+                "traffic": ncu_traffic("k_sweep", w.name, args.precision), "kernel": "k_sweep<OR> (streaming half sweep)",
                 "peak_source": peak_src, "alg_bytes_per_launch": alg, "avg_launch_us": avg * 1e6}
 
     dominant = max(prof_ms, key=prof_ms.get)
@@ -307,11 +315,12 @@ def ours(args):
         # limit is the on-chip data path, reported against the FP32 issue rate
         flops_per_update = 60.0
         n_launch = max(launches["resident"], 1)
-        avg = prof_ms["resident"] / n_launch / 1e3
+        avg = max(prof_ms["resident"] / n_launch / 1e3, 1e-12)
         alg_flops = ups * flops_per_update
         peak_alu = 152 * 128 * 2 * 2.07e9
         roof = {"bound": "alu", "achieved": alg_flops / avg / 1e12, "peak": peak_alu / 1e12, "unit": "TFLOP/s",
-                "frac": alg_flops / avg / peak_alu, "traffic": None, "kernel": "k_resident (sweep block in shared memory)",
+                "frac": alg_flops / avg / peak_alu, "traffic": ncu_traffic("k_resident", w.name, args.precision),
+                "kernel": "k_resident (sweep block in shared memory)",
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz",
                 "alg_flops_per_launch": alg_flops, "avg_launch_us": avg * 1e6,
                 "effective_hbm_GBps": ups * 36.4 / avg / 1e9}
