@@ -87,6 +87,8 @@ struct pt_engine {
     bool energy_valid = false;
     int policy = PT_POLICY_AUTO;
     bool all_resident = false;        // every sample fits the resident kernel
+    bool all_tma = false;             // every sample fits the bulk-copy half sweep
+    std::vector<int4> tma_items;
     int max_half = 0;
     uint64_t step_host = 0;           // mirror of the device step counter
 
@@ -327,6 +329,31 @@ pt_status create_impl(pt_handle* out, int n_samples, const int* Ls, const int* N
         }
         e->d.vclass_count[cls] = t - e->d.vclass_begin[cls];
     }
+    // bulk-copy (TMA) half sweep: items of P planes x up to 16 replicas
+    {
+        // PT_TMA=1 selects the bulk-copy overrelaxation half sweep (opt-in:
+        // measured slower than the vector-load kernel so far)
+        const char* ev = std::getenv("PT_TMA");
+        const bool allow = ev && std::strcmp(ev, "1") == 0;
+        e->all_tma = allow;
+        size_t smem = 0;
+        for (SampleDesc& sd : e->samples) {
+            sd.tma_planes = (!e->fp64 && sd.L % 8 == 0) ? tma_planes_for(sd.L) : 0;
+            e->all_tma = e->all_tma && sd.tma_planes > 0;
+            if (sd.tma_planes > 0) smem = std::max(smem, tma_smem_bytes(sd.tma_planes, sd.hL * sd.L));
+        }
+        if (smem > 220 * 1024) e->all_tma = false;
+        if (e->all_tma) {
+            for (const SampleDesc& sd : e->samples) {
+                const int nrep = e->C * sd.NT;
+                for (int k0 = 0; k0 < sd.L; k0 += sd.tma_planes)
+                    for (int g = 0; g < nrep; g += 16)
+                        e->tma_items.push_back(make_int4((int)(&sd - e->samples.data()), k0, sd.r0 + g,
+                                                         std::min(16, nrep - g)));
+            }
+            e->d.tma_smem = (int)smem;
+        }
+    }
     e->all_resident = true;
     for (const SampleDesc& sd : e->samples) {
         e->all_resident = e->all_resident && resident_supported(sd, e->fp64);
@@ -385,6 +412,10 @@ pt_status create_impl(pt_handle* out, int n_samples, const int* Ls, const int* N
     long long* dO; TRY(upload(e, &dO, e->chain_off)); d.chain_off = dO;
     std::vector<unsigned long long> z1(1, 0ull);
     TRY(upload(e, &d.d_step, z1));
+    std::vector<int> zerr(1, 0);
+    TRY(upload(e, &d.err, zerr));
+    int4* dTI; TRY(upload(e, &dTI, e->tma_items)); d.tma_items = dTI;
+    d.n_tma_items = (int)e->tma_items.size();
     std::vector<double> zt((size_t)t, 0.0), zq((size_t)e->sumNT * 9, 0.0), zx((size_t)e->sumNT, 0.0);
     TRY(upload(e, &d.part, zt));
     TRY(upload(e, &d.Q, zq));
@@ -436,8 +467,17 @@ pt_status create_impl(pt_handle* out, int n_samples, const int* Ls, const int* N
     return PT_OK;
 }
 
+// Synchronise the engine's stream; report a bounded device-side wait that
+// gave up since the last check (the error word is cleared).
 pt_status sync(pt_engine* e) {
     CK(e->stream ? cudaStreamSynchronize(e->stream) : cudaDeviceSynchronize());
+    int err = 0;
+    CK(cudaMemcpy(&err, e->d.err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) {
+        const int zero = 0;
+        CK(cudaMemcpy(e->d.err, &zero, sizeof(int), cudaMemcpyHostToDevice));
+        return fail(PT_ERR_TIMEOUT, "a bounded device-side wait gave up (error word %d)", err);
+    }
     return PT_OK;
 }
 
@@ -530,7 +570,10 @@ pt_status pt_sweep(pt_handle e, int n_hb, int n_or) {
     for (int o = 0; o < n_or; ++o)
         for (int c = 0; c < 2; ++c, ++k) {
             const bool last = (k == total - 1);
-            RUN(PT_KERNEL_OR, sweep_launch_count(e->d), launch_halfsweep(e->d, e->fp64, 0, last, c, k, e->stream));
+            if (e->all_tma && !last)
+                RUN(PT_KERNEL_OR, 1, launch_or_tma(e->d, c, e->stream));
+            else
+                RUN(PT_KERNEL_OR, sweep_launch_count(e->d), launch_halfsweep(e->d, e->fp64, 0, last, c, k, e->stream));
         }
     RUN(PT_KERNEL_ENERGY, 1, launch_energy_finalize(e->d, e->stream));
     RUN(PT_KERNEL_OTHER, 1, launch_advance_step(e->d, total, e->stream));

@@ -39,6 +39,10 @@ struct DevBatch {
     int exchange_cluster;           // CTAs per chain in the exchange (0: automatic)
     int exchange_impl;              // 0 automatic, 1 global-memory clusters, 2 shared-memory staged
     int max_half;                   // largest L^3/2 of the batch
+    int* err;                       // device error word (bit 0: a bounded wait gave up)
+    const int4* tma_items;          // (sample, k0, first replica, count) of the bulk-copy half sweep
+    int n_tma_items;
+    int tma_smem;                   // dynamic shared memory of the bulk-copy half sweep
     // half-sweep tiles are grouped by vector width (sites per thread)
     int vclass_begin[3], vclass_count[3], vclass_width[3];
 };
@@ -64,6 +68,13 @@ cudaError_t launch_exchange(const DevBatch& b, bool fp64, int mode, cudaStream_t
 // memory (one CTA per chain), for configurations that fit on one SM.
 bool exchange_smem_supported(int mode, int max_half, bool fp64);
 cudaError_t launch_exchange_smem(const DevBatch& b, bool fp64, int mode, int max_half, cudaStream_t st);
+
+// Overrelaxation half sweep with the slab and halo staged by bulk copies
+// (float, L % 8 == 0); tma_planes_for gives the planes per work item.
+bool tma_supported(const SampleDesc& sd, bool fp64);
+int tma_planes_for(int L);
+size_t tma_smem_bytes(int P, int plane);
+cudaError_t launch_or_tma(const DevBatch& b, int color, cudaStream_t st);
 
 // Resident sweep blocks: one CTA per replica runs n_hb + n_or sweeps in shared
 // memory and writes H[r].

@@ -38,7 +38,7 @@ struct SampleDesc {
     int tile0;                // first half-sweep tile of replica r0
     int tiles_per_rep;        // ceil(half / (TILE * vec))
     int vec;                  // sites per thread in the half sweep (4, 2 or 1)
-    int pad;
+    int tma_planes;           // z planes per item of the bulk-copy half sweep (0: not used)
 };
 
 struct ChainDesc {
