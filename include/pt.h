@@ -128,6 +128,12 @@ pt_status pt_create_batch(pt_handle *out, int n_samples, const int *L,
  * followed by a colour-1 half sweep (checkerboard order).  n_hb, n_or >= 0. */
 pt_status pt_sweep(pt_handle h, int n_hb, int n_or);
 
+/* Like pt_sweep with a per-sample number of overrelaxation sweeps:
+ * n_or[s] (host int [n_samples], >= 0) for sample s, e.g. the paper's 5L/4
+ * in a batch of uneven L.  The step counter advances as for
+ * pt_sweep(n_hb, max_s n_or[s]). */
+pt_status pt_sweep_samples(pt_handle h, int n_hb, const int *n_or);
+
 /* Enqueue one tempering update of every chain: pairs (b, b+1) for
  * b = 0 .. n_replicas-2 in increasing beta, one after the other.
  *   mode  PT_PLAIN: accept the swap with min[1, exp((b_{i+1}-b_i)(H_{i+1}-H_i))]
@@ -250,6 +256,28 @@ pt_status pt_set_policy(pt_handle h, int policy);
  * PT_ERR_CUDA for a failed launch (text in pt_last_error). */
 pt_status pt_energy_noalloc(const void *d_spins, int precision, int L, int n_configs,
                             const float *d_couplings, double *d_energy, void *stream);
+
+/* Enqueue n_cycles update cycles: a block of local updates (n_hb heat-bath
+ * sweeps and n_or overrelaxation sweeps, or n_or_samples[s] for sample s when
+ * n_or_samples is not NULL), one tempering update with the stored cooling
+ * parameters, and with measure != 0 the overlap reduction into the engine's
+ * buffers (read them with pt_measure).  When the engine runs on its own
+ * stream and profiling is off, one cycle is captured into a CUDA graph (again
+ * whenever the arguments or the kernel paths change) and replayed n_cycles
+ * times; the chain is the same as with the individual calls. */
+pt_status pt_cycles(pt_handle h, int n_cycles, int n_hb, int n_or, const int *n_or_samples,
+                    pt_mode mode, int measure);
+
+/* Autotuner: for every lattice size of the batch, time each candidate way of
+ * running the sweeps (shared-memory resident blocks or streaming half sweeps,
+ * with 4, 2 or 1 sites per thread where the row length allows) on the batch
+ * itself, a warm-up and two blocks of n_hb + n_or sweeps each, and keep the
+ * fastest under PT_POLICY_AUTO.  The chain state (spins, energies, step
+ * counter) is restored, so tuning does not change the chain.  Optional host
+ * outputs per sample: choice[s] = vector width (+10 when resident),
+ * best_ms[s] = time of one block with the chosen path.  Allocates a temporary
+ * copy of the spins on the device. */
+pt_status pt_autotune(pt_handle h, int n_hb, int n_or, int *choice, double *best_ms);
 
 /* Release all device memory of the handle.  NULL is accepted. */
 pt_status pt_destroy(pt_handle h);

@@ -8,6 +8,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -63,6 +65,19 @@ int vec_width(int hL, bool fp64) {
 
 void ptk::set_last_error(const char* msg) { snprintf(g_err, sizeof g_err, "%s", msg); }
 
+cudaError_t ptk::ensure_smem(const void* kernel, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, size_t> done;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+    std::lock_guard<std::mutex> lock(mu);
+    size_t& have = done[{kernel, dev}];
+    if (bytes <= have) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) have = bytes;
+    return e;
+}
+
 struct pt_engine {
     int S = 0, C = 0;
     bool fp64 = false;
@@ -87,8 +102,24 @@ struct pt_engine {
     bool energy_valid = false;
     int policy = PT_POLICY_AUTO;
     bool all_resident = false;        // every sample fits the resident kernel
+    bool any_streaming = true;        // some sample runs streaming half sweeps
     bool all_tma = false;             // every sample fits the bulk-copy half sweep
     std::vector<int4> tma_items;
+    std::vector<int> stile_idx;       // streaming subset of `tiles`
+    std::vector<int> res_reps;        // replicas of resident samples
+    std::vector<int> tuned_vec;       // per sample: vector width chosen by pt_autotune (0: default)
+    std::vector<int> tuned_res;       // per sample: -1 default, 0 streaming, 1 resident (pt_autotune)
+    size_t tile_cap = 0;              // capacity of the tile and partial arrays
+    int* d_stiles = nullptr;
+    int* d_res_reps = nullptr;
+    int* d_nor = nullptr;
+    std::vector<int> nor_host;        // per-sample overrelaxation counts last uploaded
+    // captured update cycle (pt_cycles)
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    std::vector<long long> graph_key;
+    long long graph_launches[PT_KERNEL_KINDS] = {0};
+    int graph_steps = 0;
     int max_half = 0;
     uint64_t step_host = 0;           // mirror of the device step counter
 
@@ -130,6 +161,10 @@ struct pt_engine {
 
     void release() {
         if (stream) cudaStreamSynchronize(stream); else cudaDeviceSynchronize();
+        if (graph_exec) cudaGraphExecDestroy(graph_exec);
+        if (graph) cudaGraphDestroy(graph);
+        graph_exec = nullptr;
+        graph = nullptr;
         for (Rec& r : recs) { ev_pool.push_back(r.a); ev_pool.push_back(r.b); }
         recs.clear();
         for (cudaEvent_t v : ev_pool) if (v) cudaEventDestroy(v);
@@ -203,9 +238,92 @@ pt_status run(pt_engine* e, int kind, int n_kernels, F&& launcher) {
     } while (0)
 
 pt_status compute_energy(pt_engine* e) {
-    RUN(PT_KERNEL_ENERGY, sweep_launch_count(e->d), launch_energy(e->d, e->fp64, e->stream));
-    RUN(PT_KERNEL_ENERGY, 1, launch_energy_finalize(e->d, e->stream));
+    RUN(PT_KERNEL_ENERGY, energy_launch_count(e->d, true), launch_energy(e->d, e->fp64, true, e->stream));
+    RUN(PT_KERNEL_ENERGY, 1, launch_energy_finalize(e->d, true, e->stream));
     e->energy_valid = true;
+    return PT_OK;
+}
+
+// Which path each sample takes: resident when the policy allows it and the
+// replica fits (or pt_autotune chose it), else streaming half sweeps.
+void choose_paths(pt_engine* e) {
+    e->all_resident = true;
+    for (size_t s = 0; s < e->samples.size(); ++s) {
+        SampleDesc& sd = e->samples[s];
+        const int def_vec = vec_width(sd.hL, e->fp64);
+        const int vec = (!e->tuned_vec.empty() && e->tuned_vec[s] > 0) ? e->tuned_vec[s] : def_vec;
+        const bool fits = resident_supported(sd, e->fp64, vec) || resident_supported(sd, e->fp64, def_vec);
+        e->all_resident = e->all_resident && fits;
+        bool res;
+        if (e->policy == PT_POLICY_STREAMING) res = false;
+        else if (e->policy == PT_POLICY_RESIDENT) res = fits;
+        else res = (!e->tuned_res.empty() && e->tuned_res[s] >= 0) ? (e->tuned_res[s] == 1 && fits) : fits;
+        sd.resident = res ? 1 : 0;
+        sd.vec = res ? (resident_supported(sd, e->fp64, vec) ? vec : def_vec) : vec;
+        sd.tiles_per_rep = (sd.half + TILE * sd.vec - 1) / (TILE * sd.vec);
+    }
+}
+
+// (Re)build the tile lists (all samples grouped by vector width, and the
+// streaming subset), the resident replica list, and upload them with the
+// sample descriptors.
+pt_status rebuild_lists(pt_engine* e) {
+    const int widths[3] = {4, 2, 1};
+    e->tiles.clear();
+    e->stile_idx.clear();
+    e->res_reps.clear();
+    int t = 0;
+    DevBatch& d = e->d;
+    for (int cls = 0; cls < 3; ++cls) {
+        d.vclass_begin[cls] = t;
+        d.vclass_width[cls] = widths[cls];
+        for (SampleDesc& sd : e->samples) {
+            if (sd.vec != widths[cls]) continue;
+            sd.tile0 = t;
+            const int nrep = e->C * sd.NT;
+            for (int q = 0; q < nrep; ++q)
+                for (int k = 0; k < sd.tiles_per_rep; ++k) {
+                    e->tiles.push_back(make_int2(sd.r0 + q, k * TILE * sd.vec));
+                    ++t;
+                }
+        }
+        d.vclass_count[cls] = t - d.vclass_begin[cls];
+    }
+    for (int cls = 0; cls < 3; ++cls) {
+        d.sclass_begin[cls] = (int)e->stile_idx.size();
+        for (const SampleDesc& sd : e->samples) {
+            if (sd.vec != widths[cls] || sd.resident) continue;
+            const int n = e->C * sd.NT * sd.tiles_per_rep;
+            for (int q = 0; q < n; ++q) e->stile_idx.push_back(sd.tile0 + q);
+        }
+        d.sclass_count[cls] = (int)e->stile_idx.size() - d.sclass_begin[cls];
+    }
+    d.res_max_half = 0;
+    e->any_streaming = false;
+    for (const SampleDesc& sd : e->samples) {
+        if (sd.resident) {
+            for (int q = 0; q < e->C * sd.NT; ++q) e->res_reps.push_back(sd.r0 + q);
+            d.res_max_half = std::max(d.res_max_half, sd.half);
+        } else {
+            e->any_streaming = true;
+        }
+    }
+    if ((size_t)t > e->tile_cap) return fail(PT_ERR_STATE, "tile list exceeds its capacity");
+    e->T = t;
+    d.n_tiles = t;
+    d.n_res_reps = (int)e->res_reps.size();
+    if (!e->tiles.empty())
+        CK(cudaMemcpyAsync((void*)d.vtiles, e->tiles.data(), sizeof(int2) * e->tiles.size(), cudaMemcpyHostToDevice,
+                           e->stream));
+    if (!e->stile_idx.empty())
+        CK(cudaMemcpyAsync(e->d_stiles, e->stile_idx.data(), sizeof(int) * e->stile_idx.size(),
+                           cudaMemcpyHostToDevice, e->stream));
+    if (!e->res_reps.empty())
+        CK(cudaMemcpyAsync(e->d_res_reps, e->res_reps.data(), sizeof(int) * e->res_reps.size(),
+                           cudaMemcpyHostToDevice, e->stream));
+    CK(cudaMemcpyAsync((void*)d.samples, e->samples.data(), sizeof(SampleDesc) * e->samples.size(),
+                       cudaMemcpyHostToDevice, e->stream));
+    CK(e->stream ? cudaStreamSynchronize(e->stream) : cudaDeviceSynchronize());
     return PT_OK;
 }
 
@@ -309,26 +427,8 @@ pt_status create_impl(pt_handle* out, int n_samples, const int* Ls, const int* N
         beta_off += NT;
         eps_off += NT - 1;
     }
-    // half-sweep tiles grouped by vector class (widths 4, 2, 1); within a
-    // class sample by sample and replica by replica, so that the tiles of a
-    // replica are contiguous
-    const int widths[3] = {4, 2, 1};
-    for (int cls = 0; cls < 3; ++cls) {
-        e->d.vclass_begin[cls] = t;
-        e->d.vclass_width[cls] = widths[cls];
-        for (int s = 0; s < n_samples; ++s) {
-            SampleDesc& sd = e->samples[s];
-            if (sd.vec != widths[cls]) continue;
-            sd.tile0 = t;
-            const int nrep = e->C * sd.NT;
-            for (int q = 0; q < nrep; ++q)
-                for (int k = 0; k < sd.tiles_per_rep; ++k) {
-                    e->tiles.push_back(make_int2(sd.r0 + q, k * TILE * sd.vec));
-                    ++t;
-                }
-        }
-        e->d.vclass_count[cls] = t - e->d.vclass_begin[cls];
-    }
+    // capacity of the tile lists: every sample at one site per thread
+    for (const SampleDesc& sd : e->samples) e->tile_cap += (size_t)e->C * sd.NT * ((sd.half + TILE - 1) / TILE);
     // bulk-copy (TMA) half sweep: items of P planes x up to 16 replicas
     {
         // PT_TMA=1 selects the bulk-copy overrelaxation half sweep (opt-in:
@@ -354,13 +454,10 @@ pt_status create_impl(pt_handle* out, int n_samples, const int* Ls, const int* N
             e->d.tma_smem = (int)smem;
         }
     }
-    e->all_resident = true;
-    for (const SampleDesc& sd : e->samples) {
-        e->all_resident = e->all_resident && resident_supported(sd, e->fp64);
-        e->max_half = std::max(e->max_half, sd.half);
-    }
+    for (const SampleDesc& sd : e->samples) e->max_half = std::max(e->max_half, sd.half);
+    choose_paths(e);
     e->R = r;
-    e->T = t;
+    e->T = 0;
     e->P = pair;
     e->sumNT = beta_off;
     e->sumEps = eps_off;
@@ -407,7 +504,15 @@ pt_status create_impl(pt_handle* out, int n_samples, const int* Ls, const int* N
     SampleDesc* dS; TRY(upload(e, &dS, e->samples)); d.samples = dS;
     ChainDesc* dC; TRY(upload(e, &dC, e->chains)); d.chains = dC;
     int4* dR; TRY(upload(e, &dR, e->reps)); d.reps = dR;
-    int2* dT; TRY(upload(e, &dT, e->tiles)); d.vtiles = dT;
+    {
+        std::vector<int2> zt2(e->tile_cap, make_int2(0, 0));
+        std::vector<int> zti(e->tile_cap, 0), zr((size_t)r, 0), zn((size_t)n_samples, 0);
+        int2* dT; TRY(upload(e, &dT, zt2)); d.vtiles = dT;
+        TRY(upload(e, &e->d_stiles, zti)); d.stiles = e->d_stiles;
+        TRY(upload(e, &e->d_res_reps, zr)); d.res_reps = e->d_res_reps;
+        TRY(upload(e, &e->d_nor, zn));
+        d.nor_s = nullptr;
+    }
     int* dQs; TRY(upload(e, &dQs, e->q_sample)); d.q_sample = dQs;
     long long* dO; TRY(upload(e, &dO, e->chain_off)); d.chain_off = dO;
     std::vector<unsigned long long> z1(1, 0ull);
@@ -416,7 +521,7 @@ pt_status create_impl(pt_handle* out, int n_samples, const int* Ls, const int* N
     TRY(upload(e, &d.err, zerr));
     int4* dTI; TRY(upload(e, &dTI, e->tma_items)); d.tma_items = dTI;
     d.n_tma_items = (int)e->tma_items.size();
-    std::vector<double> zt((size_t)t, 0.0), zq((size_t)e->sumNT * 9, 0.0), zx((size_t)e->sumNT, 0.0);
+    std::vector<double> zt(e->tile_cap, 0.0), zq((size_t)e->sumNT * 9, 0.0), zx((size_t)e->sumNT, 0.0);
     TRY(upload(e, &d.part, zt));
     TRY(upload(e, &d.Q, zq));
     TRY(upload(e, &d.chi, zx));
@@ -425,7 +530,6 @@ pt_status create_impl(pt_handle* out, int n_samples, const int* Ls, const int* N
     d.n_samples = e->S;
     d.n_chains = (int)e->chains.size();
     d.n_reps = r;
-    d.n_tiles = t;
     d.n_q = e->sumNT;
     d.max_NT = 0;
     for (int v : e->NT) d.max_NT = std::max(d.max_NT, v);
@@ -452,7 +556,9 @@ pt_status create_impl(pt_handle* out, int n_samples, const int* Ls, const int* N
     d.max_half = 0;
     for (const SampleDesc& sd : e->samples) d.max_half = std::max(d.max_half, sd.half);
 
-    st = run(e, PT_KERNEL_OTHER, 1, [&]() { return launch_init_spins(d, e->fp64, e->start, e->stream); });
+    st = rebuild_lists(e);
+    if (st == PT_OK)
+        st = run(e, PT_KERNEL_OTHER, 1, [&]() { return launch_init_spins(d, e->fp64, e->start, e->stream); });
     if (st == PT_OK) st = compute_energy(e);
     if (st == PT_OK) {
         cudaError_t ce = e->stream ? cudaStreamSynchronize(e->stream) : cudaDeviceSynchronize();
@@ -548,42 +654,72 @@ pt_status pt_create_batch(pt_handle* out, int n_samples, const int* L, const int
     return create_impl(out, n_samples, L, n_replicas, couplings, betas, opt);
 }
 
-pt_status pt_sweep(pt_handle e, int n_hb, int n_or) {
-    if (!e) return fail(PT_ERR_ARG, "NULL handle");
-    if (n_hb < 0 || n_or < 0) return fail(PT_ERR_ARG, "n_hb, n_or must be >= 0");
+// One block of local updates.  nor == NULL: n_or sweeps for every sample;
+// else nor[s] sweeps for sample s (n_or = their maximum).  Heat-bath half
+// sweeps take the step counters 0 .. 2 n_hb - 1, overrelaxation half sweeps
+// the following ones, whatever path a sample takes; the counter advances by
+// 2 (n_hb + n_or).
+static pt_status sweep_impl(pt_engine* e, int n_hb, int n_or, const int* nor) {
     const int total = 2 * (n_hb + n_or);
     if (total == 0) return PT_OK;
-    const bool resident = e->policy == PT_POLICY_RESIDENT || (e->policy == PT_POLICY_AUTO && e->all_resident);
-    if (resident) {
-        RUN(PT_KERNEL_RESIDENT, 1, launch_resident(e->d, e->fp64, n_hb, n_or, e->max_half, e->stream));
-        RUN(PT_KERNEL_OTHER, 1, launch_advance_step(e->d, total, e->stream));
-        e->step_host += (uint64_t)total;
-        e->energy_valid = true;
-        return PT_OK;
+    if (nor) {
+        if (e->nor_host.size() != (size_t)e->S || std::memcmp(e->nor_host.data(), nor, sizeof(int) * e->S) != 0) {
+            e->nor_host.assign(nor, nor + e->S);
+            CK(cudaMemcpyAsync(e->d_nor, e->nor_host.data(), sizeof(int) * e->S, cudaMemcpyHostToDevice, e->stream));
+            CK(e->stream ? cudaStreamSynchronize(e->stream) : cudaDeviceSynchronize());
+        }
+        e->d.nor_s = e->d_nor;
+    } else {
+        e->d.nor_s = nullptr;
     }
-    int k = 0;
-    for (int hb = 0; hb < n_hb; ++hb)
-        for (int c = 0; c < 2; ++c, ++k) {
-            const bool last = (k == total - 1);
-            RUN(PT_KERNEL_HB, sweep_launch_count(e->d), launch_halfsweep(e->d, e->fp64, 1, last, c, k, e->stream));
-        }
-    for (int o = 0; o < n_or; ++o)
-        for (int c = 0; c < 2; ++c, ++k) {
-            const bool last = (k == total - 1);
-            if (e->all_tma && !last)
-                RUN(PT_KERNEL_OR, 1, launch_or_tma(e->d, c, e->stream));
-            else
-                RUN(PT_KERNEL_OR, sweep_launch_count(e->d), launch_halfsweep(e->d, e->fp64, 0, last, c, k, e->stream));
-        }
-    RUN(PT_KERNEL_ENERGY, 1, launch_energy_finalize(e->d, e->stream));
+    const bool fuse = (nor == nullptr);  // per-sample counts: energies after the block
+    if (!e->res_reps.empty())
+        RUN(PT_KERNEL_RESIDENT, 1, launch_resident(e->d, e->fp64, n_hb, n_or, e->stream));
+    if (e->any_streaming) {
+        const int nl = sweep_stream_launch_count(e->d);
+        const bool tma = e->all_tma && e->res_reps.empty() && nor == nullptr;
+        int k = 0;
+        for (int hb = 0; hb < n_hb; ++hb)
+            for (int c = 0; c < 2; ++c, ++k) {
+                const bool last = fuse && (k == total - 1);
+                RUN(PT_KERNEL_HB, nl, launch_halfsweep(e->d, e->fp64, 1, last, c, k, -1, e->stream));
+            }
+        for (int o = 0; o < n_or; ++o)
+            for (int c = 0; c < 2; ++c, ++k) {
+                const bool last = fuse && (k == total - 1);
+                if (tma && !last)
+                    RUN(PT_KERNEL_OR, 1, launch_or_tma(e->d, c, e->stream));
+                else
+                    RUN(PT_KERNEL_OR, nl, launch_halfsweep(e->d, e->fp64, 0, last, c, k, o, e->stream));
+            }
+        if (!fuse)
+            RUN(PT_KERNEL_ENERGY, energy_launch_count(e->d, false), launch_energy(e->d, e->fp64, false, e->stream));
+        RUN(PT_KERNEL_ENERGY, 1, launch_energy_finalize(e->d, false, e->stream));
+    }
     RUN(PT_KERNEL_OTHER, 1, launch_advance_step(e->d, total, e->stream));
     e->step_host += (uint64_t)total;
     e->energy_valid = true;
     return PT_OK;
 }
 
-pt_status pt_exchange(pt_handle e, pt_mode mode, const float* eps) {
+pt_status pt_sweep(pt_handle e, int n_hb, int n_or) {
     if (!e) return fail(PT_ERR_ARG, "NULL handle");
+    if (n_hb < 0 || n_or < 0) return fail(PT_ERR_ARG, "n_hb, n_or must be >= 0");
+    return sweep_impl(e, n_hb, n_or, nullptr);
+}
+
+pt_status pt_sweep_samples(pt_handle e, int n_hb, const int* n_or) {
+    if (!e || !n_or) return fail(PT_ERR_ARG, "NULL argument");
+    if (n_hb < 0) return fail(PT_ERR_ARG, "n_hb must be >= 0");
+    int mx = 0;
+    for (int s = 0; s < e->S; ++s) {
+        if (n_or[s] < 0) return fail(PT_ERR_ARG, "n_or[%d] < 0", s);
+        mx = std::max(mx, n_or[s]);
+    }
+    return sweep_impl(e, n_hb, mx, n_or);
+}
+
+static pt_status exchange_impl(pt_engine* e, pt_mode mode, const float* eps) {
     if (mode != PT_PLAIN && mode != PT_DECIMATION && mode != PT_COOLHEAT) return fail(PT_ERR_ARG, "bad mode %d", (int)mode);
     if (eps) {
         pt_status st = check_eps(e, eps);
@@ -603,6 +739,198 @@ pt_status pt_exchange(pt_handle e, pt_mode mode, const float* eps) {
     RUN(PT_KERNEL_OTHER, 1, launch_advance_step(e->d, 1, e->stream));
     e->step_host += 1;
     return PT_OK;
+}
+pt_status pt_exchange(pt_handle e, pt_mode mode, const float* eps) {
+    if (!e) return fail(PT_ERR_ARG, "NULL handle");
+    return exchange_impl(e, mode, eps);
+}
+
+// n_cycles update cycles (sweep block, tempering update, and with `measure`
+// the overlap reduction), as one captured CUDA graph replayed n_cycles times
+// when the engine has its own stream and no per-kernel profiling is on; the
+// graph is captured again whenever the arguments or the kernel paths change.
+pt_status pt_cycles(pt_handle e, int n_cycles, int n_hb, int n_or, const int* n_or_samples, pt_mode mode,
+                    int measure) {
+    if (!e) return fail(PT_ERR_ARG, "NULL handle");
+    if (n_cycles < 0 || n_hb < 0 || n_or < 0) return fail(PT_ERR_ARG, "negative count");
+    if (mode != PT_PLAIN && mode != PT_DECIMATION && mode != PT_COOLHEAT) return fail(PT_ERR_ARG, "bad mode %d", (int)mode);
+    if (measure && e->C != 2) return fail(PT_ERR_STATE, "overlap needs n_copies == 2");
+    if (n_cycles == 0) return PT_OK;
+    int mx = n_or;
+    if (n_or_samples) {
+        mx = 0;
+        for (int s = 0; s < e->S; ++s) {
+            if (n_or_samples[s] < 0) return fail(PT_ERR_ARG, "n_or_samples[%d] < 0", s);
+            mx = std::max(mx, n_or_samples[s]);
+        }
+    }
+    if (mode == PT_COOLHEAT) {
+        pt_status st = check_eps(e, e->eps_host.data());
+        if (st != PT_OK) return st;
+    }
+    if (!e->energy_valid) {
+        pt_status st = compute_energy(e);
+        if (st != PT_OK) return st;
+    }
+    auto one_cycle = [&]() -> pt_status {
+        pt_status st = sweep_impl(e, n_hb, mx, n_or_samples);
+        if (st == PT_OK) st = exchange_impl(e, mode, nullptr);
+        if (st == PT_OK && measure) st = run(e, PT_KERNEL_MEASURE, 1, [&]() { return launch_overlap(e->d, e->fp64, e->stream); });
+        return st;
+    };
+    if (!e->stream || e->profiling) {
+        for (int c = 0; c < n_cycles; ++c) {
+            pt_status st = one_cycle();
+            if (st != PT_OK) return st;
+        }
+        return PT_OK;
+    }
+    if (n_or_samples &&
+        (e->nor_host.size() != (size_t)e->S || std::memcmp(e->nor_host.data(), n_or_samples, sizeof(int) * e->S) != 0)) {
+        e->nor_host.assign(n_or_samples, n_or_samples + e->S);
+        CK(cudaMemcpyAsync(e->d_nor, e->nor_host.data(), sizeof(int) * e->S, cudaMemcpyHostToDevice, e->stream));
+        CK(cudaStreamSynchronize(e->stream));
+    }
+    std::vector<long long> key = {n_hb, mx, n_or_samples ? 1 : 0, (long long)mode, measure, e->policy, e->T,
+                                  (long long)e->res_reps.size()};
+    if (n_or_samples) key.insert(key.end(), n_or_samples, n_or_samples + e->S);
+    if (!e->graph_exec || key != e->graph_key) {
+        if (e->graph_exec) cudaGraphExecDestroy(e->graph_exec);
+        if (e->graph) cudaGraphDestroy(e->graph);
+        e->graph_exec = nullptr;
+        e->graph = nullptr;
+        long long before[PT_KERNEL_KINDS];
+        std::memcpy(before, e->launches, sizeof before);
+        const uint64_t step_before = e->step_host;
+        CK(cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeRelaxed));
+        pt_status st = one_cycle();
+        cudaGraph_t g = nullptr;
+        cudaError_t ce = cudaStreamEndCapture(e->stream, &g);
+        if (st != PT_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (ce != cudaSuccess) return fail(PT_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ce));
+        e->graph = g;
+        CK(cudaGraphInstantiate(&e->graph_exec, g, 0));
+        for (int k = 0; k < PT_KERNEL_KINDS; ++k) {
+            e->graph_launches[k] = e->launches[k] - before[k];
+            e->launches[k] = before[k];
+        }
+        e->graph_steps = (int)(e->step_host - step_before);
+        e->step_host = step_before;
+        e->graph_key = key;
+    }
+    for (int c = 0; c < n_cycles; ++c) {
+        CK(cudaGraphLaunch(e->graph_exec, e->stream));
+        for (int k = 0; k < PT_KERNEL_KINDS; ++k) e->launches[k] += e->graph_launches[k];
+        e->step_host += (uint64_t)e->graph_steps;
+    }
+    e->energy_valid = true;
+    return PT_OK;
+}
+
+// Time the candidate paths (resident / streaming) and vector widths of every
+// lattice size of the batch on the batch itself and keep the fastest; the
+// chain state (spins, energies, step counter) is restored afterwards.
+pt_status pt_autotune(pt_handle e, int n_hb, int n_or, int* choice, double* best_ms) {
+    if (!e) return fail(PT_ERR_ARG, "NULL handle");
+    if (n_hb < 0 || n_or < 0 || n_hb + n_or == 0) return fail(PT_ERR_ARG, "need a positive sweep count");
+    pt_status st = sync(e);
+    if (st != PT_OK) return st;
+    const bool saved_prof = e->profiling;
+    e->profiling = false;
+    void* backup = nullptr;
+    const size_t pool_bytes = e->pool_elems * e->esz();
+    cudaError_t ce = cudaMalloc(&backup, pool_bytes + sizeof(double) * e->R);
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        e->profiling = saved_prof;
+        return fail(PT_ERR_NOMEM, "autotune backup: %s", cudaGetErrorString(ce));
+    }
+    const uint64_t step0 = e->step_host;
+    const bool ev0 = e->energy_valid;
+    CK(cudaMemcpyAsync(backup, e->d.spins, pool_bytes, cudaMemcpyDeviceToDevice, e->stream));
+    CK(cudaMemcpyAsync((char*)backup + pool_bytes, e->d.H, sizeof(double) * e->R, cudaMemcpyDeviceToDevice, e->stream));
+    const int saved_policy = e->policy;
+    e->policy = PT_POLICY_AUTO;
+    e->tuned_vec.assign(e->S, 0);
+    e->tuned_res.assign(e->S, -1);
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    std::vector<int> Ls;
+    for (const SampleDesc& sd : e->samples)
+        if (std::find(Ls.begin(), Ls.end(), sd.L) == Ls.end()) Ls.push_back(sd.L);
+    std::vector<double> best(e->S, 0.0);
+    for (int L : Ls) {
+        const int hL = L / 2;
+        std::vector<std::pair<int, int>> cand;  // (resident, vec)
+        for (int res = 1; res >= 0; --res)
+            for (int vec : {4, 2, 1}) {
+                if (e->fp64 && vec == 4) continue;
+                if (hL % vec) continue;
+                if (res) {
+                    bool ok = true;
+                    for (const SampleDesc& sd : e->samples)
+                        if (sd.L == L && !resident_supported(sd, e->fp64, vec)) ok = false;
+                    if (!ok) continue;
+                }
+                cand.push_back({res, vec});
+            }
+        double best_t = 1e30;
+        std::pair<int, int> best_c = cand.empty() ? std::make_pair(0, 1) : cand[0];
+        for (auto c : cand) {
+            for (int s = 0; s < e->S; ++s)
+                if (e->samples[s].L == L) {
+                    e->tuned_res[s] = c.first;
+                    e->tuned_vec[s] = c.second;
+                }
+            choose_paths(e);
+            st = rebuild_lists(e);
+            if (st == PT_OK) st = sweep_impl(e, n_hb, n_or, nullptr);  // warm-up
+            if (st != PT_OK) break;
+            CK(cudaEventRecord(a, e->stream));
+            for (int rep = 0; rep < 2 && st == PT_OK; ++rep) st = sweep_impl(e, n_hb, n_or, nullptr);
+            CK(cudaEventRecord(b, e->stream));
+            CK(cudaEventSynchronize(b));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, a, b));
+            if (ms < best_t) {
+                best_t = ms;
+                best_c = c;
+            }
+        }
+        if (st != PT_OK) break;
+        for (int s = 0; s < e->S; ++s)
+            if (e->samples[s].L == L) {
+                e->tuned_res[s] = best_c.first;
+                e->tuned_vec[s] = best_c.second;
+                best[s] = best_t / 2;
+            }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (st == PT_OK) {
+        choose_paths(e);
+        st = rebuild_lists(e);
+    }
+    // restore the chain state
+    cudaMemcpyAsync(e->d.spins, backup, pool_bytes, cudaMemcpyDeviceToDevice, e->stream);
+    cudaMemcpyAsync(e->d.H, (char*)backup + pool_bytes, sizeof(double) * e->R, cudaMemcpyDeviceToDevice, e->stream);
+    e->step_host = step0;
+    cudaMemcpyAsync(e->d.d_step, &e->step_host, sizeof(uint64_t), cudaMemcpyHostToDevice, e->stream);
+    cudaStreamSynchronize(e->stream);
+    cudaFree(backup);
+    e->energy_valid = ev0;
+    e->profiling = saved_prof;
+    if (saved_policy != PT_POLICY_AUTO) e->policy = PT_POLICY_AUTO;
+    if (st != PT_OK) return st;
+    for (int s = 0; s < e->S; ++s) {
+        if (choice) choice[s] = e->samples[s].resident ? 10 + e->samples[s].vec : e->samples[s].vec;
+        if (best_ms) best_ms[s] = best[s];
+    }
+    return sync(e);
 }
 
 pt_status pt_measure(pt_handle e, double* energy, double* overlap, double* chi) {
@@ -855,8 +1183,11 @@ pt_status pt_set_policy(pt_handle e, int policy) {
         return fail(PT_ERR_ARG, "bad policy %d", policy);
     if (policy == PT_POLICY_RESIDENT && !e->all_resident)
         return fail(PT_ERR_STATE, "a sample does not fit the resident sweep kernel");
+    pt_status st = sync(e);
+    if (st != PT_OK) return st;
     e->policy = policy;
-    return PT_OK;
+    choose_paths(e);
+    return rebuild_lists(e);
 }
 
 pt_status pt_destroy(pt_handle e) {

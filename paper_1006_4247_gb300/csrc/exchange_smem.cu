@@ -301,21 +301,21 @@ cudaError_t launch_exchange_smem(const DevBatch& b, bool fp64, int mode, int max
     cudaError_t e;
     if (mode == 2) {
         if (fp64) {
-            e = cudaFuncSetAttribute(k_exchange_coolheat_smem<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            e = ensure_smem((const void*)k_exchange_coolheat_smem<double>, smem);
             if (e != cudaSuccess) return e;
             k_exchange_coolheat_smem<double><<<b.n_chains, SX_THREADS, smem, st>>>(b);
         } else {
-            e = cudaFuncSetAttribute(k_exchange_coolheat_smem<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            e = ensure_smem((const void*)k_exchange_coolheat_smem<float>, smem);
             if (e != cudaSuccess) return e;
             k_exchange_coolheat_smem<float><<<b.n_chains, SX_THREADS, smem, st>>>(b);
         }
     } else {
         if (fp64) {
-            e = cudaFuncSetAttribute(k_exchange_decimation_smem<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            e = ensure_smem((const void*)k_exchange_decimation_smem<double>, smem);
             if (e != cudaSuccess) return e;
             k_exchange_decimation_smem<double><<<b.n_chains, SX_THREADS, smem, st>>>(b);
         } else {
-            e = cudaFuncSetAttribute(k_exchange_decimation_smem<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            e = ensure_smem((const void*)k_exchange_decimation_smem<float>, smem);
             if (e != cudaSuccess) return e;
             k_exchange_decimation_smem<float><<<b.n_chains, SX_THREADS, smem, st>>>(b);
         }

@@ -7,6 +7,10 @@
 
 namespace ptk {
 
+// Raise a kernel's dynamic shared-memory limit once per kernel, device and
+// size (later launches of the same or a smaller size skip the call).
+cudaError_t ensure_smem(const void* kernel, size_t bytes);
+
 // Everything a kernel may need about the batch; pointers are device pointers.
 struct DevBatch {
     void* spins;                    // float or double pool (see pt_types.h)
@@ -24,7 +28,11 @@ struct DevBatch {
     const SampleDesc* samples;      // [S]
     const ChainDesc* chains;        // [chains]
     const int4* reps;               // [R] (sample, chain, b, copy*NT + b)
-    const int2* vtiles;             // [T] (replica, first h) of the half-sweep tiles
+    const int2* vtiles;             // [T] (replica, first h) of the half-sweep tiles (all samples)
+    const int* stiles;              // indices into vtiles of the streaming samples' tiles
+    const int* res_reps;            // replicas of the resident samples
+    const int* nor_s;               // per-sample overrelaxation sweeps of the current block (or NULL)
+    int n_res_reps, res_max_half;
     const int* q_sample;            // [sum NT] sample of each (sample, beta) pair
     const long long* chain_off;     // [chains] element offset of buffer 0
     unsigned long long* d_step;     // Philox step counter
@@ -43,8 +51,10 @@ struct DevBatch {
     const int4* tma_items;          // (sample, k0, first replica, count) of the bulk-copy half sweep
     int n_tma_items;
     int tma_smem;                   // dynamic shared memory of the bulk-copy half sweep
-    // half-sweep tiles are grouped by vector width (sites per thread)
+    // half-sweep tiles are grouped by vector width (sites per thread); the
+    // streaming subset is grouped the same way inside stiles
     int vclass_begin[3], vclass_count[3], vclass_width[3];
+    int sclass_begin[3], sclass_count[3];
 };
 
 // Record the text returned by pt_last_error() for the calling thread.
@@ -53,12 +63,18 @@ void set_last_error(const char* msg);
 // Number of kernels one half sweep launches (one per vector-width class).
 int sweep_launch_count(const DevBatch& b);
 
-// Half sweeps (kind 0 = overrelaxation, 1 = heat bath); `energy` also writes
-// the per-tile energy partials of the updated colour (valid for colour 1).
+// Half sweeps of the streaming samples (kind 0 = overrelaxation, 1 = heat
+// bath); `energy` also writes the per-tile energy partials of the updated
+// colour (valid for colour 1).  or_index >= 0 skips samples whose per-sample
+// overrelaxation count (nor_s) is <= or_index.
 cudaError_t launch_halfsweep(const DevBatch& b, bool fp64, int kind, bool energy, int color,
-                             int step_k, cudaStream_t st);
-cudaError_t launch_energy(const DevBatch& b, bool fp64, cudaStream_t st);
-cudaError_t launch_energy_finalize(const DevBatch& b, cudaStream_t st);
+                             int step_k, int or_index, cudaStream_t st);
+int sweep_stream_launch_count(const DevBatch& b);
+// Energy partials of every sample (all = true) or of the streaming samples.
+cudaError_t launch_energy(const DevBatch& b, bool fp64, bool all, cudaStream_t st);
+int energy_launch_count(const DevBatch& b, bool all);
+// H[r] from the partials, for every replica (all) or the streaming samples'.
+cudaError_t launch_energy_finalize(const DevBatch& b, bool all, cudaStream_t st);
 cudaError_t launch_init_spins(const DevBatch& b, bool fp64, int ordered, cudaStream_t st);
 cudaError_t launch_advance_step(const DevBatch& b, int by, cudaStream_t st);
 cudaError_t launch_overlap(const DevBatch& b, bool fp64, cudaStream_t st);
@@ -78,7 +94,7 @@ cudaError_t launch_or_tma(const DevBatch& b, int color, cudaStream_t st);
 
 // Resident sweep blocks: one CTA per replica runs n_hb + n_or sweeps in shared
 // memory and writes H[r].
-bool resident_supported(const SampleDesc& sd, bool fp64);
-cudaError_t launch_resident(const DevBatch& b, bool fp64, int n_hb, int n_or, int max_half, cudaStream_t st);
+bool resident_supported(const SampleDesc& sd, bool fp64, int vec);
+cudaError_t launch_resident(const DevBatch& b, bool fp64, int n_hb, int n_or, cudaStream_t st);
 
 }  // namespace ptk

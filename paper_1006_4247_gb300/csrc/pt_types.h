@@ -39,6 +39,8 @@ struct SampleDesc {
     int tiles_per_rep;        // ceil(half / (TILE * vec))
     int vec;                  // sites per thread in the half sweep (4, 2 or 1)
     int tma_planes;           // z planes per item of the bulk-copy half sweep (0: not used)
+    int resident;             // 1: this sample's sweeps run in the shared-memory resident kernel
+    int pad;
 };
 
 struct ChainDesc {

@@ -74,28 +74,12 @@ __device__ __forceinline__ double res_halfsweep(T* __restrict__ sm, const float*
     return e;
 }
 
-// Heat-bath half sweeps (1 of 1 + 5L/4 sweeps) run one site per thread so
-// that the register peak is set by the vectorised overrelaxation path and
-// four CTAs fit on an SM.
+// The sweep block of one replica (the CTA's replica is held in `sm`).  Heat-
+// bath half sweeps (1 of 1 + 5L/4 sweeps) run one site per thread so that the
+// register peak is set by the vectorised overrelaxation path.
 template <typename T, int V>
-__global__ void __launch_bounds__(RES_THREADS, 4) k_resident(DevBatch a, int n_hb, int n_or) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* sm = reinterpret_cast<T*>(smem_raw);
-    __shared__ double red[32];
-    const int r = blockIdx.x;
-    const int4 rd = a.reps[r];
-    const SampleDesc& sd = a.samples[rd.x];
-    const int half = sd.half;
-    const int n3 = 6 * half;  // elements of one replica
-    T* g = (T*)a.spins + a.chain_off[rd.y] + (long long)a.bufmap[r] * (long long)n3;
-    // load the replica (16-byte vectors; n3 is a multiple of the vector width)
-    constexpr int VW = 16 / sizeof(T);
-    for (int q = threadIdx.x * VW; q < n3; q += RES_THREADS * VW) {
-        T v[VW];
-        ldv<T, VW>(g + q, v);
-        stv<T, VW>(sm + q, v);
-    }
-    __syncthreads();
+__device__ __forceinline__ double res_block(T* sm, const DevBatch& a, const SampleDesc& sd, const int4& rd,
+                                            int n_hb, int n_or) {
     const float* J = a.J + sd.J_off;
     const T beta = (T)a.betas[sd.beta_off + rd.z];
     const unsigned long long step0 = *a.d_step;
@@ -112,10 +96,37 @@ __global__ void __launch_bounds__(RES_THREADS, 4) k_resident(DevBatch a, int n_h
     for (int o = 0; o < n_or; ++o)
         for (int c = 0; c < 2; ++c, ++kstep) {
             const bool last = kstep == total - 1;
-            e += res_halfsweep<T, V, 0>(sm, J, sd, c, beta, a.seed, (uint32_t)rd.x, (uint32_t)rd.w, 0ull,
-                                        last);
+            e += res_halfsweep<T, V, 0>(sm, J, sd, c, beta, a.seed, (uint32_t)rd.x, (uint32_t)rd.w, 0ull, last);
             __syncthreads();
         }
+    return e;
+}
+
+// One CTA per replica of a resident sample (a.res_reps).  The sample's row
+// width decides the vector width (4 or 2 sites per thread in float, 2 in
+// double); the overrelaxation count is per sample when a.nor_s is given.
+template <typename T>
+__global__ void __launch_bounds__(RES_THREADS, 4) k_resident(DevBatch a, int n_hb, int n_or) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sm = reinterpret_cast<T*>(smem_raw);
+    __shared__ double red[32];
+    const int r = a.res_reps[blockIdx.x];
+    const int4 rd = a.reps[r];
+    const SampleDesc& sd = a.samples[rd.x];
+    const int half = sd.half;
+    const int n3 = 6 * half;  // elements of one replica
+    const int nor = a.nor_s ? a.nor_s[rd.x] : n_or;
+    T* g = (T*)a.spins + a.chain_off[rd.y] + (long long)a.bufmap[r] * (long long)n3;
+    constexpr int VW = 16 / sizeof(T);
+    for (int q = threadIdx.x * VW; q < n3; q += RES_THREADS * VW) {
+        T v[VW];
+        ldv<T, VW>(g + q, v);
+        stv<T, VW>(sm + q, v);
+    }
+    __syncthreads();
+    double e;
+    if (sizeof(T) == 4 && sd.vec == 4) e = res_block<T, (sizeof(T) == 4 ? 4 : 2)>(sm, a, sd, rd, n_hb, nor);
+    else e = res_block<T, 2>(sm, a, sd, rd, n_hb, nor);
     for (int q = threadIdx.x * VW; q < n3; q += RES_THREADS * VW) {
         T v[VW];
         ldv<T, VW>(sm + q, v);
@@ -127,23 +138,26 @@ __global__ void __launch_bounds__(RES_THREADS, 4) k_resident(DevBatch a, int n_h
 
 size_t resident_smem_bytes(int half, bool fp64) { return (size_t)6 * half * (fp64 ? 8 : 4); }
 
-bool resident_supported(const SampleDesc& sd, bool fp64) {
-    // float4 / double2 rows and at most 100 KB of spins per CTA (two CTAs per SM)
-    const int V = fp64 ? 2 : 4;
-    return sd.hL % V == 0 && resident_smem_bytes(sd.half, fp64) <= 100 * 1024;
+bool resident_supported(const SampleDesc& sd, bool fp64, int vec) {
+    // 16- or 8-byte rows (vec 4 or 2; double only 2) and at most 100 KB of
+    // spins per CTA (two CTAs per SM)
+    if (vec != 4 && vec != 2) return false;
+    if (fp64 && vec != 2) return false;
+    return sd.hL % vec == 0 && resident_smem_bytes(sd.half, fp64) <= 100 * 1024;
 }
 
-cudaError_t launch_resident(const DevBatch& b, bool fp64, int n_hb, int n_or, int max_half, cudaStream_t st) {
-    const size_t smem = resident_smem_bytes(max_half, fp64);
+cudaError_t launch_resident(const DevBatch& b, bool fp64, int n_hb, int n_or, cudaStream_t st) {
+    if (b.n_res_reps == 0) return cudaSuccess;
+    const size_t smem = resident_smem_bytes(b.res_max_half, fp64);
     cudaError_t e;
     if (fp64) {
-        e = cudaFuncSetAttribute(k_resident<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = ensure_smem((const void*)k_resident<double>, smem);
         if (e != cudaSuccess) return e;
-        k_resident<double, 2><<<b.n_reps, RES_THREADS, smem, st>>>(b, n_hb, n_or);
+        k_resident<double><<<b.n_res_reps, RES_THREADS, smem, st>>>(b, n_hb, n_or);
     } else {
-        e = cudaFuncSetAttribute(k_resident<float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = ensure_smem((const void*)k_resident<float>, smem);
         if (e != cudaSuccess) return e;
-        k_resident<float, 4><<<b.n_reps, RES_THREADS, smem, st>>>(b, n_hb, n_or);
+        k_resident<float><<<b.n_res_reps, RES_THREADS, smem, st>>>(b, n_hb, n_or);
     }
     return cudaGetLastError();
 }

@@ -18,12 +18,16 @@
 namespace ptk {
 
 // KIND 0: overrelaxation, 1: heat bath, 2: energy only (colour 0, no store).
+// Tiles: tile_begin + blockIdx.x indexes `tidx` (the streaming subset) when
+// it is given, else vtiles directly.
 template <typename T, int V, int KIND, bool ENERGY>
-__global__ void __launch_bounds__(TILE) k_sweep(DevBatch a, int tile_begin, int color, int step_k) {
+__global__ void __launch_bounds__(TILE) k_sweep(DevBatch a, const int* __restrict__ tidx, int tile_begin,
+                                                int color, int step_k, int or_index) {
     __shared__ double sh[32];
-    const int t = tile_begin + (int)blockIdx.x;
+    const int t = tidx ? tidx[tile_begin + (int)blockIdx.x] : tile_begin + (int)blockIdx.x;
     const int2 tl = a.vtiles[t];
     const int4 rd = a.reps[tl.x];
+    if (or_index >= 0 && a.nor_s && or_index >= a.nor_s[rd.x]) return;  // uniform per block
     const SampleDesc& sd = a.samples[rd.x];
     const int half = sd.half, hL = sd.hL, L = sd.L;
     const int h0 = tl.y + (int)threadIdx.x * V;
@@ -83,12 +87,14 @@ __global__ void __launch_bounds__(TILE) k_sweep(DevBatch a, int tile_begin, int 
     }
 }
 
-// H[r] = sum of the tile partials of replica r, in tile order.
-__global__ void k_energy_finalize(DevBatch a) {
+// H[r] = sum of the tile partials of replica r, in tile order (replicas of
+// resident samples are skipped unless `all`).
+__global__ void k_energy_finalize(DevBatch a, int all) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= a.n_reps) return;
     const int4 rd = a.reps[r];
     const SampleDesc& sd = a.samples[rd.x];
+    if (!all && sd.resident) return;
     const int t0 = sd.tile0 + (r - sd.r0) * sd.tiles_per_rep;
     double H = 0.0;
     for (int k = 0; k < sd.tiles_per_rep; ++k) H += a.part[t0 + k];
@@ -188,35 +194,37 @@ __global__ void __launch_bounds__(TILE) k_overlap(DevBatch a) {
 // Launchers
 // ---------------------------------------------------------------------------
 template <typename T, int V>
-static void sweep_tv(const DevBatch& b, int kind, bool energy, int color, int step_k, int begin, int count,
-                     cudaStream_t st) {
+static void sweep_tv(const DevBatch& b, const int* tidx, int kind, bool energy, int color, int step_k,
+                     int or_index, int begin, int count, cudaStream_t st) {
     if (count == 0) return;
     dim3 grid(count), block(TILE);
     if (kind == 1) {
-        if (energy) k_sweep<T, V, 1, true><<<grid, block, 0, st>>>(b, begin, color, step_k);
-        else k_sweep<T, V, 1, false><<<grid, block, 0, st>>>(b, begin, color, step_k);
+        if (energy) k_sweep<T, V, 1, true><<<grid, block, 0, st>>>(b, tidx, begin, color, step_k, or_index);
+        else k_sweep<T, V, 1, false><<<grid, block, 0, st>>>(b, tidx, begin, color, step_k, or_index);
     } else if (kind == 0) {
-        if (energy) k_sweep<T, V, 0, true><<<grid, block, 0, st>>>(b, begin, color, step_k);
-        else k_sweep<T, V, 0, false><<<grid, block, 0, st>>>(b, begin, color, step_k);
+        if (energy) k_sweep<T, V, 0, true><<<grid, block, 0, st>>>(b, tidx, begin, color, step_k, or_index);
+        else k_sweep<T, V, 0, false><<<grid, block, 0, st>>>(b, tidx, begin, color, step_k, or_index);
     } else {
-        k_sweep<T, V, 2, false><<<grid, block, 0, st>>>(b, begin, 0, 0);
+        k_sweep<T, V, 2, false><<<grid, block, 0, st>>>(b, tidx, begin, 0, 0, -1);
     }
 }
 
-// One launch per vector-width class present in the batch.
-static cudaError_t sweep_all(const DevBatch& b, bool fp64, int kind, bool energy, int color, int step_k,
-                             cudaStream_t st) {
+// One launch per vector-width class present in the tile set.
+static cudaError_t sweep_all(const DevBatch& b, bool fp64, bool streaming_only, int kind, bool energy, int color,
+                             int step_k, int or_index, cudaStream_t st) {
     for (int cls = 0; cls < 3; ++cls) {
-        const int begin = b.vclass_begin[cls], count = b.vclass_count[cls];
+        const int begin = streaming_only ? b.sclass_begin[cls] : b.vclass_begin[cls];
+        const int count = streaming_only ? b.sclass_count[cls] : b.vclass_count[cls];
         if (count == 0) continue;
+        const int* tidx = streaming_only ? b.stiles : nullptr;
         const int V = b.vclass_width[cls];
         if (fp64) {
-            if (V == 2) sweep_tv<double, 2>(b, kind, energy, color, step_k, begin, count, st);
-            else sweep_tv<double, 1>(b, kind, energy, color, step_k, begin, count, st);
+            if (V == 2) sweep_tv<double, 2>(b, tidx, kind, energy, color, step_k, or_index, begin, count, st);
+            else sweep_tv<double, 1>(b, tidx, kind, energy, color, step_k, or_index, begin, count, st);
         } else {
-            if (V == 4) sweep_tv<float, 4>(b, kind, energy, color, step_k, begin, count, st);
-            else if (V == 2) sweep_tv<float, 2>(b, kind, energy, color, step_k, begin, count, st);
-            else sweep_tv<float, 1>(b, kind, energy, color, step_k, begin, count, st);
+            if (V == 4) sweep_tv<float, 4>(b, tidx, kind, energy, color, step_k, or_index, begin, count, st);
+            else if (V == 2) sweep_tv<float, 2>(b, tidx, kind, energy, color, step_k, or_index, begin, count, st);
+            else sweep_tv<float, 1>(b, tidx, kind, energy, color, step_k, or_index, begin, count, st);
         }
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -224,23 +232,29 @@ static cudaError_t sweep_all(const DevBatch& b, bool fp64, int kind, bool energy
     return cudaSuccess;
 }
 
-int sweep_launch_count(const DevBatch& b) {
+int sweep_stream_launch_count(const DevBatch& b) {
     int n = 0;
-    for (int cls = 0; cls < 3; ++cls) n += b.vclass_count[cls] > 0;
+    for (int cls = 0; cls < 3; ++cls) n += b.sclass_count[cls] > 0;
+    return n;
+}
+
+int energy_launch_count(const DevBatch& b, bool all) {
+    int n = 0;
+    for (int cls = 0; cls < 3; ++cls) n += (all ? b.vclass_count[cls] : b.sclass_count[cls]) > 0;
     return n;
 }
 
 cudaError_t launch_halfsweep(const DevBatch& b, bool fp64, int kind, bool energy, int color, int step_k,
-                             cudaStream_t st) {
-    return sweep_all(b, fp64, kind, energy, color, step_k, st);
+                             int or_index, cudaStream_t st) {
+    return sweep_all(b, fp64, true, kind, energy, color, step_k, or_index, st);
 }
 
-cudaError_t launch_energy(const DevBatch& b, bool fp64, cudaStream_t st) {
-    return sweep_all(b, fp64, 2, false, 0, 0, st);
+cudaError_t launch_energy(const DevBatch& b, bool fp64, bool all, cudaStream_t st) {
+    return sweep_all(b, fp64, !all, 2, false, 0, 0, -1, st);
 }
 
-cudaError_t launch_energy_finalize(const DevBatch& b, cudaStream_t st) {
-    k_energy_finalize<<<(b.n_reps + 127) / 128, 128, 0, st>>>(b);
+cudaError_t launch_energy_finalize(const DevBatch& b, bool all, cudaStream_t st) {
+    k_energy_finalize<<<(b.n_reps + 127) / 128, 128, 0, st>>>(b, all ? 1 : 0);
     return cudaGetLastError();
 }
 

@@ -275,7 +275,7 @@ size_t tma_smem_bytes(int P, int plane) {
 cudaError_t launch_or_tma(const DevBatch& b, int color, cudaStream_t st) {
     if (b.n_tma_items == 0) return cudaSuccess;
     const size_t smem = b.tma_smem;
-    cudaError_t e = cudaFuncSetAttribute(k_or_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_smem((const void*)k_or_tma, smem);
     if (e != cudaSuccess) return e;
     const int grid = b.n_tma_items < b.n_sm ? b.n_tma_items : b.n_sm;
     k_or_tma<<<grid, TMA_THREADS, smem, st>>>(b, b.tma_items, b.n_tma_items, color);

@@ -32,7 +32,8 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 
 # Entry points declared in include/pt.h (the symbol test checks this list
 # against the header).
-ENTRY_POINTS = ["pt_options_default", "pt_create", "pt_create_batch", "pt_sweep", "pt_exchange",
+ENTRY_POINTS = ["pt_options_default", "pt_create", "pt_create_batch", "pt_sweep", "pt_sweep_samples",
+                "pt_cycles", "pt_autotune", "pt_exchange",
                 "pt_measure", "pt_measure_device", "pt_get_stats", "pt_get_spins", "pt_set_spins",
                 "pt_set_params", "pt_set_rng_step", "pt_get_rng_step", "pt_save", "pt_load",
                 "pt_profile", "pt_profile_read", "pt_set_policy", "pt_energy_noalloc", "pt_destroy",
@@ -76,6 +77,9 @@ def load_library(path: str = LIB_PATH):
                 "pt_create_batch": (ip, [C.POINTER(vp), ip, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                          C.POINTER(fp), C.POINTER(dp), C.POINTER(PtOptions)]),
                 "pt_sweep": (ip, [vp, ip, ip]),
+                "pt_sweep_samples": (ip, [vp, ip, C.POINTER(C.c_int)]),
+                "pt_cycles": (ip, [vp, ip, ip, ip, C.POINTER(C.c_int), ip, ip]),
+                "pt_autotune": (ip, [vp, ip, ip, C.POINTER(C.c_int), dp]),
                 "pt_exchange": (ip, [vp, ip, fp]),
                 "pt_measure": (ip, [vp, dp, dp, dp]),
                 "pt_measure_device": (ip, [vp, vp, vp, vp]),
@@ -149,6 +153,26 @@ def pt_create_batch(L, n_replicas, couplings, betas, opt: PtOptions | None = Non
 
 def pt_sweep(h, n_hb, n_or):
     _check(load_library().pt_sweep(h, int(n_hb), int(n_or)))
+
+
+def pt_sweep_samples(h, n_hb, n_or):
+    a = np.ascontiguousarray(n_or, np.int32)
+    _check(load_library().pt_sweep_samples(h, int(n_hb), _ptr(a, C.c_int)))
+
+
+def pt_cycles(h, n_cycles, n_hb, n_or, mode, measure=False, n_or_samples=None):
+    mode = MODES.get(mode, mode) if isinstance(mode, str) else int(mode)
+    a = None if n_or_samples is None else np.ascontiguousarray(n_or_samples, np.int32)
+    _check(load_library().pt_cycles(h, int(n_cycles), int(n_hb), int(n_or), _ptr(a, C.c_int), mode,
+                                    int(bool(measure))))
+
+
+def pt_autotune(h, n_hb, n_or, n_samples):
+    """Return (choice[S], best_ms[S]); choice = sites per thread, +10 if resident."""
+    choice = np.zeros(n_samples, np.int32)
+    best = np.zeros(n_samples)
+    _check(load_library().pt_autotune(h, int(n_hb), int(n_or), _ptr(choice, C.c_int), _ptr(best, C.c_double)))
+    return choice, best
 
 
 def pt_exchange(h, mode, eps=None):
@@ -317,6 +341,15 @@ class Engine:
 
     def exchange(self, mode="plain", eps=None):
         pt_exchange(self.h, mode, eps)
+
+    def sweep_samples(self, n_hb, n_or):
+        pt_sweep_samples(self.h, n_hb, n_or)
+
+    def cycles(self, n_cycles, n_hb=1, n_or=1, mode="plain", measure=False, n_or_samples=None):
+        pt_cycles(self.h, n_cycles, n_hb, n_or, mode, measure, n_or_samples)
+
+    def autotune(self, n_hb=1, n_or=1):
+        return pt_autotune(self.h, n_hb, n_or, self.S)
 
     def energies(self):
         out = np.zeros(self.R)

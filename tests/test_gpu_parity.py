@@ -301,7 +301,7 @@ def test_resident_and_streaming_paths_fp32():
 
 def test_policy_errors():
     from paper_1006_4247_gb300 import pt
-    eng, J, B = make_engine(12, 1, 3, 2, "fp32")
+    eng, J, B = make_engine(2, 1, 3, 2, "fp32")  # rows of one site: no resident kernel
     with pytest.raises(pt.PtError) as ei:
         eng.set_policy("resident")
     assert ei.value.status == pt.PT_ERR_STATE
