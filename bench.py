@@ -43,12 +43,14 @@ def parse():
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
-    p.add_argument("--workload", default="L16_R24_S64")
+    p.add_argument("--workload", default="L16_R24_S64",
+                   choices=["L4_R8_S1", "L16_R24_S64", "L32_R48_S16", "uneven_S256"])
     p.add_argument("--exchange", default=None)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     p.add_argument("--policy", default="auto", choices=["auto", "streaming", "resident"])
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     return p.parse_args()
 
@@ -151,6 +153,10 @@ class ClockSampler:
 
 
 def workload_of(args, rank):
+    if args.workload == "uneven_S256":
+        w = W.uneven_batch()
+        w.j_seed0 += 100000 * rank
+        return w
     w = W.WORKLOADS[args.workload]()
     if args.exchange:
         w.exchange = args.exchange
@@ -158,8 +164,16 @@ def workload_of(args, rank):
     return w
 
 
+def n_or_of(w):
+    """Overrelaxation sweeps per sample: the workload's count, or 5L/4 per
+    sample (section IV) for a batch of uneven L."""
+    if "n_or_per_L" in w.extra:
+        return [w.extra["n_or_per_L"][L] for L in w.L]
+    return [w.n_or] * w.n_samples
+
+
 def updates_per_step(w):
-    return sum(w.n_copies * nt * L ** 3 for L, nt in zip(w.L, w.n_replicas)) * (w.n_hb + w.n_or)
+    return sum(w.n_copies * nt * L ** 3 * (w.n_hb + no) for L, nt, no in zip(w.L, w.n_replicas, n_or_of(w)))
 
 
 def eps_array(w):
@@ -239,33 +253,48 @@ def ours(args):
         dist.init_process_group("nccl")
     _build.build()
     w = workload_of(args, rank)
-    stream = torch.cuda.current_stream()
-    Js = np.stack(w.couplings())
-    Bs = np.stack(w.betas())
-    eng = pt.Engine(w.L[0], Js, Bs, n_copies=w.n_copies, precision=args.precision, seed=7 + rank,
-                    stream=stream.cuda_stream)
+    stream = torch.cuda.Stream()  # the engine's own stream (graphs need one)
+    uniform = len(set(w.L)) == 1 and len(set(w.n_replicas)) == 1
+    if uniform:
+        eng = pt.Engine(w.L[0], np.stack(w.couplings()), np.stack(w.betas()), n_copies=w.n_copies,
+                        precision=args.precision, seed=7 + rank, stream=stream.cuda_stream)
+    else:
+        eng = pt.Engine(list(w.L), w.couplings(), w.betas(), n_copies=w.n_copies, precision=args.precision,
+                        seed=7 + rank, stream=stream.cuda_stream)
     eps = eps_array(w)
     eng.set_params(eps=eps)
-    eng.set_policy(args.policy)
     mode = w.exchange
+    nor = n_or_of(w)
+    nor_samples = None if len(set(nor)) == 1 else nor
+    tune = None
+    if args.policy == "auto" and not args.no_autotune:
+        tune = eng.autotune(w.n_hb, min(max(min(nor), 1), 4))
+    else:
+        eng.set_policy(args.policy)
 
-    def step():
-        eng.sweep(w.n_hb, w.n_or)
-        eng.exchange(mode)
-        eng.measure_device()
+    def step(graph=True):
+        if graph:
+            eng.cycles(1, w.n_hb, nor[0], mode, measure=True, n_or_samples=nor_samples)
+        else:
+            if nor_samples is None:
+                eng.sweep(w.n_hb, nor[0])
+            else:
+                eng.sweep_samples(w.n_hb, nor_samples)
+            eng.exchange(mode)
+            eng.measure_device()
 
     def barrier():
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    def timed(nsteps):
-        eng.profile(True)
+    def timed(nsteps, profile):
+        eng.profile(profile)
         barrier()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
         for _ in range(nsteps):
-            step()
+            step(graph=not profile)
         ev1.record(stream)
         barrier()
         t = ev0.elapsed_time(ev1)
@@ -279,74 +308,98 @@ def ours(args):
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
-    ms, prof_ms, launches = timed(args.steps)
+    ms, _, launches = timed(args.steps, profile=False)
     clk = clocks.stop()
+    # a shorter profiled pass (events around every launch) for per-kernel times
+    _, prof_ms, prof_launches = timed(max(2, args.steps // 2), profile=True)
     if world > 1:
         t = torch.tensor([ms], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
     ups = updates_per_step(w)
     value = ups * args.steps * world / (ms * 1e6)
+    n_prof_steps = max(2, args.steps // 2)
 
-    NT, L, S, C = w.n_replicas[0], w.L[0], w.n_samples, w.n_copies
-    N = L ** 3
-    R = S * C * NT
     bpe = 4 if args.precision == "fp32" else 8
     peak, peak_src = load_peaks()
+    resident = [bool(tune is not None and tune[0][s] >= 10) for s in range(w.n_samples)] if tune is not None \
+        else [args.policy == "resident"] * w.n_samples
+    if tune is None and args.policy == "auto":
+        resident = [False] * w.n_samples
 
-    def or_roofline(pm, ln):
-        """HBM roofline of the streaming overrelaxation half sweep: 36 B per
-        update in float (read own + write own + read the other colour), plus
-        the sample's couplings once per half sweep."""
-        alg = R * (N // 2) * 9 * bpe + S * 3 * N * 4
-        avg = pm["or"] / max(ln["or"], 1) / 1e3
-        if avg <= 0:  # no event time (e.g. launches serialised by a profiler)
+    def or_roofline(pm, ln, res_flags, steps):
+        """HBM roofline of the streaming overrelaxation half sweeps: 36 B per
+        update in float (read own + write own + read the other colour) plus
+        each sample's couplings once per half sweep."""
+        alg = 0
+        for s, (L, nt, no) in enumerate(zip(w.L, w.n_replicas, nor)):
+            if res_flags[s]:
+                continue
+            N = L ** 3
+            alg += (w.n_copies * nt * (N // 2) * 9 * bpe + 3 * N * 4) * 2 * no
+        alg *= steps
+        if pm["or"] <= 0 or alg == 0:  # no event time (e.g. launches serialised by a profiler)
             return None
-        ach = alg / avg / 1e9
+        ach = alg / (pm["or"] / 1e3) / 1e9
+        n_launch = max(ln["or"], 1)
+        kern = "k_sweep"
+        wl = w.name if uniform else None
         return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                "traffic": ncu_traffic("k_sweep", w.name, args.precision), "kernel": "k_sweep<OR> (streaming half sweep)",
-                "peak_source": peak_src, "alg_bytes_per_launch": alg, "avg_launch_us": avg * 1e6}
+                "traffic": ncu_traffic(kern, wl, args.precision) if wl else None,
+                "kernel": "k_sweep<OR> (streaming half sweep)", "peak_source": peak_src,
+                "alg_bytes_per_launch": alg / n_launch, "avg_launch_us": pm["or"] / n_launch * 1e3}
 
-    dominant = max(prof_ms, key=prof_ms.get)
+    def resident_roofline(pm, ln, res_flags, steps):
+        """The resident block reads and writes each replica once per cycle; its
+        limit is the on-chip data path, reported against the FP32 issue rate
+        (152 SMs x 128 lanes x 2 FLOP x 2.07 GHz) with 60 FLOP counted per
+        site update."""
+        upd = sum(w.n_copies * nt * L ** 3 * (w.n_hb + no)
+                  for s, (L, nt, no) in enumerate(zip(w.L, w.n_replicas, nor)) if res_flags[s]) * steps
+        if pm["resident"] <= 0 or upd == 0:
+            return None
+        t = pm["resident"] / 1e3
+        peak_alu = 152 * 128 * 2 * 2.07e9
+        n_launch = max(ln["resident"], 1)
+        return {"bound": "alu", "achieved": upd * 60.0 / t / 1e12, "peak": peak_alu / 1e12, "unit": "TFLOP/s",
+                "frac": upd * 60.0 / t / peak_alu,
+                "traffic": ncu_traffic("k_resident", w.name, args.precision) if uniform else None,
+                "kernel": "k_resident (sweep block in shared memory)",
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz",
+                "alg_flops_per_launch": upd * 60.0 / n_launch, "avg_launch_us": t / n_launch * 1e6,
+                "effective_hbm_GBps": upd * 36.4 / t / 1e9}
+
+    dominant = max(("or", "resident"), key=lambda k: prof_ms.get(k, 0.0))
     share = {k: v / max(sum(prof_ms.values()), 1e-9) for k, v in prof_ms.items()}
     streaming = None
     if dominant == "resident":
-        # the resident block reads and writes each replica once per cycle; its
-        # limit is the on-chip data path, reported against the FP32 issue rate
-        flops_per_update = 60.0
-        n_launch = max(launches["resident"], 1)
-        avg = max(prof_ms["resident"] / n_launch / 1e3, 1e-12)
-        alg_flops = ups * flops_per_update
-        peak_alu = 152 * 128 * 2 * 2.07e9
-        roof = {"bound": "alu", "achieved": alg_flops / avg / 1e12, "peak": peak_alu / 1e12, "unit": "TFLOP/s",
-                "frac": alg_flops / avg / peak_alu, "traffic": ncu_traffic("k_resident", w.name, args.precision),
-                "kernel": "k_resident (sweep block in shared memory)",
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz",
-                "alg_flops_per_launch": alg_flops, "avg_launch_us": avg * 1e6,
-                "effective_hbm_GBps": ups * 36.4 / avg / 1e9}
-        eng.set_policy("streaming")
-        for _ in range(2):
-            step()
-        _, pm2, ln2 = timed(max(2, args.steps // 2))
-        streaming = or_roofline(pm2, ln2)
-        eng.set_policy(args.policy)
+        roof = resident_roofline(prof_ms, prof_launches, resident, n_prof_steps)
+        if uniform and all(resident):
+            # the HBM roofline of the streaming half sweep on the same workload
+            eng.set_policy("streaming")
+            for _ in range(2):
+                step(graph=False)
+            _, pm2, ln2 = timed(max(2, args.steps // 2), profile=True)
+            streaming = or_roofline(pm2, ln2, [False] * w.n_samples, max(2, args.steps // 2))
+            eng.set_policy(args.policy)  # back to the tuned paths for the end-to-end pass
     else:
-        roof = or_roofline(prof_ms, launches)
+        roof = or_roofline(prof_ms, prof_launches, resident, n_prof_steps)
 
     # end to end through the public API with host buffers
+    R = sum(w.n_copies * n for n in w.n_replicas)
+    SNT = sum(w.n_replicas)
     e2e = None
     if not args.no_e2e:
-        B_h = torch.from_numpy(Bs.reshape(-1).copy()).pin_memory()
+        B_h = torch.from_numpy(np.concatenate(w.betas()).copy()).pin_memory()
         E_h = torch.from_numpy(eps.copy()).pin_memory()
         Hh = torch.empty(R, dtype=torch.float64).pin_memory()
-        Qh = torch.empty(S * NT * 9, dtype=torch.float64).pin_memory()
-        Xh = torch.empty(S * NT, dtype=torch.float64).pin_memory()
+        Qh = torch.empty(SNT * 9, dtype=torch.float64).pin_memory()
+        Xh = torch.empty(SNT, dtype=torch.float64).pin_memory()
         Bn, En, Hn, Qn, Xn = (t.numpy() for t in (B_h, E_h, Hh, Qh, Xh))
 
         def e2e_step():
             eng.set_params(Bn, En)
-            eng.sweep(w.n_hb, w.n_or)
-            eng.exchange(mode)
+            eng.cycles(1, w.n_hb, nor[0], mode, measure=False, n_or_samples=nor_samples)
             pt.pt_measure(eng.h, Hn, Qn, Xn)
 
         for _ in range(2):
@@ -369,24 +422,30 @@ def ours(args):
     if rank == 0 and world == 1 and not args.no_cpu:
         v, n, el = oracle_cycle_rate(w)
         cpu = {"value": v, "unit": "updates/ns", "cores": 1, "kind": "oracle",
-               "sample": f"{n} cycles of one sample (L={L}, {NT} replicas x {C} copies, "
-                         f"1 HB + {w.n_or} OR + {mode}) in {el:.1f} s, single thread"}
+               "sample": f"{n} cycles of one sample (L={w.L[0]}, {w.n_replicas[0]} replicas x {w.n_copies} copies, "
+                         f"1 HB + {nor[0]} OR + {mode}) in {el:.1f} s, single thread"}
 
-    spins_bytes = eng.R * N * 3 * bpe
+    spins_bytes = sum(w.n_copies * nt * L ** 3 * 3 * bpe for L, nt in zip(w.L, w.n_replicas))
     if rank == 0:
+        cfg = {"workload": w.name, "samples": w.n_samples, "copies": w.n_copies, "n_hb": w.n_hb,
+               "exchange": mode, "eps": w.eps, "precision": args.precision, "policy": args.policy,
+               "autotune": None if tune is None else {"choice": [int(c) for c in tune[0]][:8],
+                                                      "resident_samples": int(sum(resident))},
+               "graph": True, "parallelism": f"samples sharded x{world}",
+               "l2": f"inputs larger than L2 ({spins_bytes / 1e6:.0f} MB of spins > 129 MB)"}
+        if uniform:
+            cfg.update({"L": w.L[0], "replicas": w.n_replicas[0], "n_or": nor[0]})
+        else:
+            cfg.update({"L": sorted(set(w.L)), "replicas": [min(w.n_replicas), max(w.n_replicas)],
+                        "n_or": "5L/4 per sample"})
         line = {
             "metric": "site_updates_per_ns", "value": value, "unit": "updates/ns", "n_gpus": world,
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
-            "config": {"workload": w.name, "L": L, "samples": S, "replicas": NT, "copies": C,
-                       "n_hb": w.n_hb, "n_or": w.n_or, "exchange": mode, "eps": w.eps,
-                       "precision": args.precision, "policy": args.policy,
-                       "parallelism": f"samples sharded x{world}",
-                       "l2": f"inputs larger than L2 ({spins_bytes / 1e6:.0f} MB of spins > 129 MB)"},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "streaming_roofline": streaming,
+            "config": cfg, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "streaming_roofline": streaming,
             "gpu_launches": int(sum(launches.values())), "clocks": clk,
-            "kernel_share": share, "kernel_ms": prof_ms, "kernel_launches": launches,
+            "kernel_share": share, "kernel_ms_profiled": prof_ms, "kernel_launches_profiled": prof_launches,
         }
         print(json.dumps(line), flush=True)
     eng.close()

@@ -41,7 +41,8 @@
  * handle usable, except after PT_ERR_CUDA caused by a sticky CUDA error.
  *
  * Ordering: calls that only enqueue device work (pt_sweep, pt_exchange,
- * pt_set_rng_step) return before the work completes; calls that return host
+ * pt_set_params, pt_cycles, pt_measure_device) return before the work
+ * completes; calls that return host
  * data (pt_measure, pt_get_stats, pt_get_spins, pt_save) synchronise the
  * engine's stream first.
  */
@@ -180,7 +181,9 @@ pt_status pt_set_spins(pt_handle h, int sample, int copy, int replica, const dou
 
 /* Replace the inverse temperatures (host double, same layout as at creation)
  * and/or the cooling parameters (host float [n_samples][n_replicas-1]); either
- * may be NULL. */
+ * may be NULL.  The values are validated, staged in pinned memory owned by the
+ * engine and copied on the engine's stream (ordered before later work); the
+ * call does not synchronise and the caller's arrays may be reused at once. */
 pt_status pt_set_params(pt_handle h, const double *betas, const float *eps);
 
 /* Set / read the Philox step counter. */

@@ -114,6 +114,11 @@ struct pt_engine {
     int* d_res_reps = nullptr;
     int* d_nor = nullptr;
     std::vector<int> nor_host;        // per-sample overrelaxation counts last uploaded
+    // pinned staging buffers for host parameters (two, used in turn; the
+    // event of a buffer marks the end of its last copy)
+    struct Staging { void* host = nullptr; size_t bytes = 0; cudaEvent_t ev = nullptr; };
+    Staging stage[2];
+    int stage_next = 0;
     // captured update cycle (pt_cycles)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
@@ -161,6 +166,11 @@ struct pt_engine {
 
     void release() {
         if (stream) cudaStreamSynchronize(stream); else cudaDeviceSynchronize();
+        for (Staging& st : stage) {
+            if (st.host) cudaFreeHost(st.host);
+            if (st.ev) cudaEventDestroy(st.ev);
+            st = Staging();
+        }
         if (graph_exec) cudaGraphExecDestroy(graph_exec);
         if (graph) cudaGraphDestroy(graph);
         graph_exec = nullptr;
@@ -237,6 +247,27 @@ pt_status run(pt_engine* e, int kind, int n_kernels, F&& launcher) {
         if (st_ != PT_OK) return st_;                                    \
     } while (0)
 
+// Copy host data to the device on the engine's stream without waiting: the
+// bytes go through a pinned staging buffer, so the caller may reuse its array
+// as soon as this returns.
+pt_status stage_copy(pt_engine* e, void* dst, const void* src, size_t bytes) {
+    pt_engine::Staging& st = e->stage[e->stage_next];
+    e->stage_next ^= 1;
+    if (st.ev) CK(cudaEventSynchronize(st.ev));
+    else CK(cudaEventCreateWithFlags(&st.ev, cudaEventDisableTiming));
+    if (st.bytes < bytes) {
+        if (st.host) cudaFreeHost(st.host);
+        st.host = nullptr;
+        st.bytes = 0;
+        CK(cudaMallocHost(&st.host, bytes));
+        st.bytes = bytes;
+    }
+    std::memcpy(st.host, src, bytes);
+    CK(cudaMemcpyAsync(dst, st.host, bytes, cudaMemcpyHostToDevice, e->stream));
+    CK(cudaEventRecord(st.ev, e->stream));
+    return PT_OK;
+}
+
 pt_status compute_energy(pt_engine* e) {
     RUN(PT_KERNEL_ENERGY, energy_launch_count(e->d, true), launch_energy(e->d, e->fp64, true, e->stream));
     RUN(PT_KERNEL_ENERGY, 1, launch_energy_finalize(e->d, true, e->stream));
@@ -309,6 +340,8 @@ pt_status rebuild_lists(pt_engine* e) {
         }
     }
     if ((size_t)t > e->tile_cap) return fail(PT_ERR_STATE, "tile list exceeds its capacity");
+    // every sample streaming: the subset is the whole list, index it directly
+    d.stiles = e->res_reps.empty() ? nullptr : e->d_stiles;
     e->T = t;
     d.n_tiles = t;
     d.n_res_reps = (int)e->res_reps.size();
@@ -725,8 +758,8 @@ static pt_status exchange_impl(pt_engine* e, pt_mode mode, const float* eps) {
         pt_status st = check_eps(e, eps);
         if (st != PT_OK) return st;
         std::memcpy(e->eps_host.data(), eps, sizeof(float) * e->eps_host.size());
-        CK(cudaMemcpyAsync((void*)e->d.eps, e->eps_host.data(), sizeof(float) * e->eps_host.size(),
-                           cudaMemcpyHostToDevice, e->stream));
+        pt_status st2 = stage_copy(e, (void*)e->d.eps, eps, sizeof(float) * e->eps_host.size());
+        if (st2 != PT_OK) return st2;
     } else if (mode == PT_COOLHEAT) {
         pt_status st = check_eps(e, e->eps_host.data());
         if (st != PT_OK) return st;
@@ -1044,16 +1077,21 @@ pt_status pt_set_params(pt_handle e, const double* betas, const float* eps) {
                 if (b > 0 && !(v > betas[sd.beta_off + b - 1])) return fail(PT_ERR_ARG, "sample %d: betas not increasing", s);
             }
         }
-        CK(cudaMemcpyAsync((void*)e->d.betas, betas, sizeof(double) * e->sumNT, cudaMemcpyHostToDevice, e->stream));
     }
     if (eps) {
         for (int q = 0; q < e->sumEps; ++q)
             if (!std::isfinite(eps[q]) || eps[q] < 0.f) return fail(PT_ERR_EPS, "eps[%d] invalid", q);
-        std::memcpy(e->eps_host.data(), eps, sizeof(float) * e->eps_host.size());
-        CK(cudaMemcpyAsync((void*)e->d.eps, e->eps_host.data(), sizeof(float) * e->sumEps, cudaMemcpyHostToDevice,
-                           e->stream));
     }
-    return sync(e);
+    if (betas) {
+        pt_status st = stage_copy(e, (void*)e->d.betas, betas, sizeof(double) * e->sumNT);
+        if (st != PT_OK) return st;
+    }
+    if (eps) {
+        std::memcpy(e->eps_host.data(), eps, sizeof(float) * e->eps_host.size());
+        pt_status st = stage_copy(e, (void*)e->d.eps, eps, sizeof(float) * e->sumEps);
+        if (st != PT_OK) return st;
+    }
+    return PT_OK;
 }
 
 pt_status pt_set_rng_step(pt_handle e, uint64_t step) {

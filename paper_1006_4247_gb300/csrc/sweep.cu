@@ -216,7 +216,7 @@ static cudaError_t sweep_all(const DevBatch& b, bool fp64, bool streaming_only, 
         const int begin = streaming_only ? b.sclass_begin[cls] : b.vclass_begin[cls];
         const int count = streaming_only ? b.sclass_count[cls] : b.vclass_count[cls];
         if (count == 0) continue;
-        const int* tidx = streaming_only ? b.stiles : nullptr;
+        const int* tidx = streaming_only ? b.stiles : nullptr;  // NULL stiles: subset == whole list
         const int V = b.vclass_width[cls];
         if (fp64) {
             if (V == 2) sweep_tv<double, 2>(b, tidx, kind, energy, color, step_k, or_index, begin, count, st);
