@@ -285,6 +285,96 @@ pt_status pt_autotune(pt_handle h, int n_hb, int n_or, int *choice, double *best
 /* Release all device memory of the handle.  NULL is accepted. */
 pt_status pt_destroy(pt_handle h);
 
+/* ---------------------------------------------------------------------------
+ * Learned ladder.  A perceptron 4 -> 64 -> 64 -> 2P+1 (ReLU hidden layers,
+ * bfloat16 weights, float accumulation, float master weights) maps the
+ * description of a sample to the parameters of its tempering: the shape of
+ * the inverse-temperature ladder, the cooling/heating parameter epsilon of
+ * every pair and the number of replicas the range needs.  Sec. 2.3 motivates it (the best epsilon depends on the pair of
+ * temperatures and decreases with beta_{i+1}/beta_i; one epsilon for all
+ * pairs was the paper's simplification), and Sec. 4 suggests tuning epsilon
+ * per pair.  The net only chooses parameters: the chain is exact for every
+ * ladder.  The paper has no network; the design is this library's.
+ *
+ * Features x (float [4] per row): ln L, beta_min, beta_max, and the coupling
+ * statistic g = mean_x sqrt(sum_y J_xy^2) / (sqrt(6) rms J).
+ * Outputs z (float [2P+1] per row), with P knots u_k = k / P:
+ *   d_k = softplus(z_k) + PT_MLP_SHAPE_FLOOR, f_k = d_k / sum_j d_j,
+ *   F(u_k) = sum_{j<k} f_j, F linear between knots (F(u) = u is the
+ *   geometric ladder; the floor keeps every ladder strictly ascending);
+ *   ln beta_i = ln beta_min + F(i / (NT - 1)) ln(beta_max / beta_min);
+ *   e_k = sigmoid(z_{P+k}), kappa(u) = kappa_max e(u), e linear between the
+ *   knot midpoints (k + 1/2) / P, constant beyond the outer ones;
+ *   eps_i = kappa((i + 1/2) / (NT - 1)) (ln beta_{i+1} - ln beta_i);
+ *   Lambda = exp(z_{2P}), the predicted sum over the pairs of an
+ *   equal-acceptance ladder of the width sigma of the Gaussian log acceptance
+ *   ratio (acceptance erfc(sigma / 2^{3/2})); NT = 1 + ceil(Lambda /
+ *   sigma_target) replicas give each pair the acceptance of sigma_target.
+ * Targets t (float [2P+1] per row): t_k = target f_k (summing to 1),
+ * t_{P+k} = target e_k in (0, 1), t_{2P} = target ln Lambda.  Loss of a row:
+ *   (1/P) sum_k [ (P (f_k - t_k))^2 + w_kappa (e_k - t_{P+k})^2 ]
+ *   + (z_{2P} - t_{2P})^2,
+ * averaged over the batch.  Parameters (float, pt_mlp_num_params of them):
+ * [W1 64x4 | b1 64 | W2 64x64 | b2 64 | W3 (2P+1)x64 | b3 2P+1], W[out][in].
+ * All arrays of these calls are HOST arrays; the calls copy them to and from
+ * the device and synchronise the handle's stream before returning.
+ * ------------------------------------------------------------------------- */
+#define PT_MLP_IN 4
+#define PT_MLP_HIDDEN 64
+#define PT_MLP_MAX_KNOTS 64
+#define PT_MLP_SHAPE_FLOOR 0.01f
+typedef struct pt_mlp *pt_mlp_handle;
+
+/* Create a net with n_knots (1..PT_MLP_MAX_KNOTS) knots on the given
+ * cudaStream_t (NULL: legacy stream).  Weights are initialised from seed
+ * (splitmix64, uniform in +-1/sqrt(fan_in), the last layer scaled by 0.01 so
+ * that a fresh net proposes a nearly geometric ladder); biases are zero.
+ * Errors: PT_ERR_ARG, PT_ERR_NOMEM, PT_ERR_CUDA. */
+pt_status pt_mlp_create(pt_mlp_handle *out, int n_knots, uint64_t seed, void *stream);
+
+/* Number of float parameters (0 for NULL). */
+int pt_mlp_num_params(pt_mlp_handle h);
+
+/* Replace the master weights (host float [num_params]) and refresh the
+ * bfloat16 copy; the Adam moments and step count are reset.  PT_ERR_ARG for
+ * a non-finite value. */
+pt_status pt_mlp_set_params(pt_mlp_handle h, const float *params);
+
+/* Read the master weights (float) and/or the bfloat16 copy used by the
+ * products (raw bits); either pointer may be NULL. */
+pt_status pt_mlp_get_params(pt_mlp_handle h, float *params, uint16_t *bf16);
+
+/* Forward pass of batch rows: x float [batch][4] -> z float [batch][2P+1]. */
+pt_status pt_mlp_forward(pt_mlp_handle h, int batch, const float *x, float *z);
+
+/* Loss and its gradient with respect to the master weights (float
+ * [num_params], computed through the bfloat16 weights).  loss or grad may be
+ * NULL.  w_kappa >= 0 weights the epsilon part of the loss. */
+pt_status pt_mlp_loss_grad(pt_mlp_handle h, int batch, const float *x, const float *target, float w_kappa,
+                           float *loss, float *grad);
+
+/* steps full-batch Adam steps (beta1 0.9, beta2 0.999, eps 1e-8, learning
+ * rate lr) on the device.  losses (float [steps], may be NULL) receives the
+ * loss before each step; asking for it synchronises every step. */
+pt_status pt_mlp_train(pt_mlp_handle h, int batch, const float *x, const float *target, float w_kappa, int steps,
+                       float lr, float *losses);
+
+/* Ladders proposed for batch rows.  Row r has n_temps[r] inverse
+ * temperatures between beta_min[r] and beta_max[r] (0 < beta_min < beta_max),
+ * written to betas[r * stride + i] (double, strictly ascending, exactly
+ * beta_min and beta_max at the ends), and n_temps[r] - 1 values epsilon to
+ * eps[r * (stride - 1) + i] (float); unused entries are zero.  n_temps is in
+ * and out: 2 <= n_temps[r] <= stride is used as given; n_temps[r] <= 0 asks
+ * the net, NT = 1 + ceil(Lambda / sigma_target) clamped to [2, stride], and
+ * the count chosen is written back (sigma_target > 0 is then required).
+ * kappa_max >= 0 scales the epsilon outputs.  stride >= 2. */
+pt_status pt_mlp_ladder(pt_mlp_handle h, int batch, const float *x, const double *beta_min, const double *beta_max,
+                        int *n_temps, int stride, float kappa_max, double sigma_target, double *betas,
+                        float *eps);
+
+/* Release the net.  NULL is accepted. */
+pt_status pt_mlp_destroy(pt_mlp_handle h);
+
 /* Text of the calling thread's last error ("" if none). */
 const char *pt_last_error(void);
 

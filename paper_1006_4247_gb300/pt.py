@@ -37,7 +37,9 @@ ENTRY_POINTS = ["pt_options_default", "pt_create", "pt_create_batch", "pt_sweep"
                 "pt_measure", "pt_measure_device", "pt_get_stats", "pt_get_spins", "pt_set_spins",
                 "pt_set_params", "pt_set_rng_step", "pt_get_rng_step", "pt_save", "pt_load",
                 "pt_profile", "pt_profile_read", "pt_set_policy", "pt_energy_noalloc", "pt_destroy",
-                "pt_last_error"]
+                "pt_last_error", "pt_mlp_create", "pt_mlp_num_params", "pt_mlp_set_params",
+                "pt_mlp_get_params", "pt_mlp_forward", "pt_mlp_loss_grad", "pt_mlp_train", "pt_mlp_ladder",
+                "pt_mlp_destroy"]
 PT_KERNEL_KINDS = 7
 KERNEL_KINDS = ["hb", "or", "energy", "exchange", "measure", "other", "resident"]
 PT_POLICY_AUTO, PT_POLICY_STREAMING, PT_POLICY_RESIDENT = 0, 1, 2
@@ -97,6 +99,15 @@ def load_library(path: str = LIB_PATH):
                 "pt_load": (ip, [vp, C.c_char_p]),
                 "pt_destroy": (ip, [vp]),
                 "pt_last_error": (C.c_char_p, []),
+                "pt_mlp_create": (ip, [C.POINTER(vp), ip, C.c_uint64, vp]),
+                "pt_mlp_num_params": (ip, [vp]),
+                "pt_mlp_set_params": (ip, [vp, fp]),
+                "pt_mlp_get_params": (ip, [vp, fp, C.POINTER(C.c_uint16)]),
+                "pt_mlp_forward": (ip, [vp, ip, fp, fp]),
+                "pt_mlp_loss_grad": (ip, [vp, ip, fp, fp, C.c_float, fp, fp]),
+                "pt_mlp_train": (ip, [vp, ip, fp, fp, C.c_float, ip, C.c_float, fp]),
+                "pt_mlp_ladder": (ip, [vp, ip, fp, dp, dp, C.POINTER(C.c_int), ip, C.c_float, C.c_double, dp, fp]),
+                "pt_mlp_destroy": (ip, [vp]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -438,3 +449,117 @@ class Engine:
 
     def __exit__(self, *a):
         self.close()
+
+
+# ---------------------------------------------------------------- learned ladder
+MLP_IN, MLP_HIDDEN, MLP_MAX_KNOTS = 4, 64, 64
+
+
+def mlp_num_params(n_knots: int) -> int:
+    """Size of the float parameter vector of a net with n_knots knots."""
+    N = 2 * n_knots + 1
+    return MLP_HIDDEN * MLP_IN + MLP_HIDDEN + MLP_HIDDEN * MLP_HIDDEN + MLP_HIDDEN + N * MLP_HIDDEN + N
+
+
+class Mlp:
+    """The ladder network behind pt_mlp_* (argument marshalling only)."""
+
+    def __init__(self, n_knots: int, seed: int = 1, stream=None):
+        lib = load_library()
+        h = C.c_void_p()
+        s = None if stream is None else C.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+        _check(lib.pt_mlp_create(C.byref(h), int(n_knots), C.c_uint64(seed), s))
+        self.h = h
+        self.n_knots = int(n_knots)
+        self.n_params = lib.pt_mlp_num_params(h)
+
+    @staticmethod
+    def _rows(x):
+        x = np.ascontiguousarray(x, np.float32)
+        if x.ndim != 2 or x.shape[1] != MLP_IN:
+            raise ValueError(f"features must be [batch, {MLP_IN}]")
+        return x
+
+    def _targets(self, x, t):
+        t = np.ascontiguousarray(t, np.float32)
+        if t.shape != (x.shape[0], 2 * self.n_knots + 1):
+            raise ValueError(f"targets must be [batch, {2 * self.n_knots + 1}]")
+        return t
+
+    def params(self):
+        """(master float32 [n], bfloat16 bits uint16 [n])."""
+        p = np.zeros(self.n_params, np.float32)
+        b = np.zeros(self.n_params, np.uint16)
+        _check(load_library().pt_mlp_get_params(self.h, _ptr(p, C.c_float), _ptr(b, C.c_uint16)))
+        return p, b
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, np.float32)
+        if p.shape != (self.n_params,):
+            raise ValueError(f"expected {self.n_params} parameters")
+        _check(load_library().pt_mlp_set_params(self.h, _ptr(p, C.c_float)))
+
+    def forward(self, x):
+        x = self._rows(x)
+        z = np.zeros((x.shape[0], 2 * self.n_knots + 1), np.float32)
+        _check(load_library().pt_mlp_forward(self.h, x.shape[0], _ptr(x, C.c_float), _ptr(z, C.c_float)))
+        return z
+
+    def loss_grad(self, x, t, w_kappa=1.0):
+        x = self._rows(x)
+        t = self._targets(x, t)
+        loss = C.c_float()
+        g = np.zeros(self.n_params, np.float32)
+        _check(load_library().pt_mlp_loss_grad(self.h, x.shape[0], _ptr(x, C.c_float), _ptr(t, C.c_float),
+                                               C.c_float(w_kappa), C.byref(loss), _ptr(g, C.c_float)))
+        return float(loss.value), g
+
+    def train(self, x, t, steps, lr=1e-3, w_kappa=1.0, record=False):
+        """Full-batch Adam on the device; returns the per-step losses when
+        record is set (one synchronisation per step), else None."""
+        x = self._rows(x)
+        t = self._targets(x, t)
+        losses = np.zeros(max(int(steps), 1), np.float32) if record else None
+        _check(load_library().pt_mlp_train(self.h, x.shape[0], _ptr(x, C.c_float), _ptr(t, C.c_float),
+                                           C.c_float(w_kappa), int(steps), C.c_float(lr),
+                                           _ptr(losses, C.c_float)))
+        return None if losses is None else losses[:int(steps)]
+
+    def ladder(self, x, beta_min, beta_max, n_temps, kappa_max, sigma_target=0.0, max_temps=512):
+        """Per row: (betas float64 [NT], eps float32 [NT - 1]).  n_temps <= 0
+        lets the net choose NT for the acceptance of sigma_target (at most
+        max_temps)."""
+        x = self._rows(x)
+        B = x.shape[0]
+        bmin = np.ascontiguousarray(np.broadcast_to(beta_min, (B,)), np.float64)
+        bmax = np.ascontiguousarray(np.broadcast_to(beta_max, (B,)), np.float64)
+        nt = np.array(np.broadcast_to(n_temps, (B,)), np.int32)
+        stride = int(max(nt.max(), max_temps if (nt <= 0).any() else 2))
+        betas = np.zeros((B, stride), np.float64)
+        eps = np.zeros((B, stride - 1), np.float32)
+        _check(load_library().pt_mlp_ladder(self.h, B, _ptr(x, C.c_float), _ptr(bmin, C.c_double),
+                                            _ptr(bmax, C.c_double), _ptr(nt, C.c_int), stride,
+                                            C.c_float(kappa_max), C.c_double(sigma_target),
+                                            _ptr(betas, C.c_double), _ptr(eps, C.c_float)))
+        return [(betas[r, :nt[r]].copy(), eps[r, :nt[r] - 1].copy()) for r in range(B)]
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            pt_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def pt_mlp_destroy(h):
+    _check(load_library().pt_mlp_destroy(h))
