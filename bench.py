@@ -32,6 +32,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_1006_4247_gb300 import sharding  # noqa: E402
 from paper_1006_4247_gb300 import workloads as W  # noqa: E402
 
 HBM_FALLBACK_GBS = 6800.0
@@ -155,12 +156,12 @@ class ClockSampler:
 def workload_of(args, rank):
     if args.workload == "uneven_S256":
         w = W.uneven_batch()
-        w.j_seed0 += 100000 * rank
+        w.j_seed0 = sharding.coupling_seed0(w.j_seed0, rank)
         return w
     w = W.WORKLOADS[args.workload]()
     if args.exchange:
         w.exchange = args.exchange
-    w.j_seed0 += 100000 * rank
+    w.j_seed0 = sharding.coupling_seed0(w.j_seed0, rank)
     return w
 
 
@@ -257,10 +258,10 @@ def ours(args):
     uniform = len(set(w.L)) == 1 and len(set(w.n_replicas)) == 1
     if uniform:
         eng = pt.Engine(w.L[0], np.stack(w.couplings()), np.stack(w.betas()), n_copies=w.n_copies,
-                        precision=args.precision, seed=7 + rank, stream=stream.cuda_stream)
+                        precision=args.precision, seed=sharding.engine_seed(rank), stream=stream.cuda_stream)
     else:
         eng = pt.Engine(list(w.L), w.couplings(), w.betas(), n_copies=w.n_copies, precision=args.precision,
-                        seed=7 + rank, stream=stream.cuda_stream)
+                        seed=sharding.engine_seed(rank), stream=stream.cuda_stream)
     eps = eps_array(w)
     eng.set_params(eps=eps)
     mode = w.exchange
@@ -284,9 +285,7 @@ def ours(args):
             eng.measure_device()
 
     def barrier():
-        if world > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize()
+        sharding.barrier(torch.cuda.synchronize)
 
     def timed(nsteps, profile):
         eng.profile(profile)
@@ -312,12 +311,9 @@ def ours(args):
     clk = clocks.stop()
     # a shorter profiled pass (events around every launch) for per-kernel times
     _, prof_ms, prof_launches = timed(max(2, args.steps // 2), profile=True)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = sharding.max_over_ranks(ms, device="cuda")
     ups = updates_per_step(w)
-    value = ups * args.steps * world / (ms * 1e6)
+    value = sharding.weak_throughput(ups, args.steps, world, ms, 1e6)
     n_prof_steps = max(2, args.steps // 2)
 
     bpe = 4 if args.precision == "fp32" else 8
@@ -410,11 +406,8 @@ def ours(args):
             e2e_step()
         barrier()
         el = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([el], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            el = float(t.item())
-        e2e = {"value": ups * args.steps * world / (el * 1e9), "unit": "updates/ns",
+        el = sharding.max_over_ranks(el, device="cuda")
+        e2e = {"value": sharding.weak_throughput(ups, args.steps, world, el, 1e9), "unit": "updates/ns",
                "h2d_bytes_per_step": int(Bn.nbytes + En.nbytes),
                "d2h_bytes_per_step": int(Hn.nbytes + Qn.nbytes + Xn.nbytes)}
 

@@ -21,17 +21,19 @@ namespace ptk {
 
 constexpr int RES_THREADS = 256;
 
-template <typename T, int V, int KIND>
-__device__ __forceinline__ double res_halfsweep(T* __restrict__ sm, const float* __restrict__ J,
-                                                const SampleDesc& sd, int color, T beta,
-                                                unsigned long long seed, uint32_t sample,
-                                                uint32_t rep_id, unsigned long long step, bool energy) {
+// ENERGY (compile time, only the block's last half sweep) also returns the
+// thread's share of H in the spin precision: a few sites per thread, so at
+// most a few float terms meet before the block reduction carries on in double.
+template <typename T, int V, int KIND, bool ENERGY>
+__device__ __forceinline__ T res_halfsweep(T* __restrict__ sm, const float* __restrict__ J, const SampleDesc& sd,
+                                           int color, T beta, unsigned long long seed, uint32_t sample,
+                                           uint32_t rep_id, unsigned long long step) {
     const int half = sd.half, hL = sd.hL, L = sd.L;
     T* own = sm + color * 3 * half;
     const T* oth = sm + (1 - color) * 3 * half;
     const float* Jown = J + color * 3 * half;
     const float* Joth = J + (1 - color) * 3 * half;
-    double e = 0.0;
+    T e = (T)0;
     for (int h0 = (int)threadIdx.x * V; h0 < half; h0 += RES_THREADS * V) {
         const int row = (int)fdiv((uint32_t)h0, sd.div_hL);
         const int ih0 = h0 - row * hL;
@@ -66,7 +68,7 @@ __device__ __forceinline__ double res_halfsweep(T* __restrict__ sm, const float*
                 or_site(Sv, sv);
             }
             s[0][v] = sv.x; s[1][v] = sv.y; s[2][v] = sv.z;
-            if (energy) e -= (double)dot(sv, Sv);
+            if (ENERGY) e -= dot(sv, Sv);
         }
 #pragma unroll
         for (int c = 0; c < 3; ++c) stv<T, V>(own + c * half + h0, s[c]);
@@ -78,25 +80,29 @@ __device__ __forceinline__ double res_halfsweep(T* __restrict__ sm, const float*
 // bath half sweeps (1 of 1 + 5L/4 sweeps) run one site per thread so that the
 // register peak is set by the vectorised overrelaxation path.
 template <typename T, int V>
-__device__ __forceinline__ double res_block(T* sm, const DevBatch& a, const SampleDesc& sd, const int4& rd,
-                                            int n_hb, int n_or) {
+__device__ __forceinline__ T res_block(T* sm, const DevBatch& a, const SampleDesc& sd, const int4& rd, int n_hb,
+                                       int n_or) {
     const float* J = a.J + sd.J_off;
     const T beta = (T)a.betas[sd.beta_off + rd.z];
     const unsigned long long step0 = *a.d_step;
     const int total = 2 * (n_hb + n_or);
-    double e = 0.0;
+    T e = (T)0;
     int kstep = 0;
     for (int hb = 0; hb < n_hb; ++hb)
         for (int c = 0; c < 2; ++c, ++kstep) {
-            const bool last = kstep == total - 1;
-            e += res_halfsweep<T, 1, 1>(sm, J, sd, c, beta, a.seed, (uint32_t)rd.x, (uint32_t)rd.w,
-                                        step0 + (unsigned long long)kstep, last);
+            const unsigned long long st = step0 + (unsigned long long)kstep;
+            if (kstep == total - 1)
+                e = res_halfsweep<T, 1, 1, true>(sm, J, sd, c, beta, a.seed, (uint32_t)rd.x, (uint32_t)rd.w, st);
+            else
+                res_halfsweep<T, 1, 1, false>(sm, J, sd, c, beta, a.seed, (uint32_t)rd.x, (uint32_t)rd.w, st);
             __syncthreads();
         }
     for (int o = 0; o < n_or; ++o)
         for (int c = 0; c < 2; ++c, ++kstep) {
-            const bool last = kstep == total - 1;
-            e += res_halfsweep<T, V, 0>(sm, J, sd, c, beta, a.seed, (uint32_t)rd.x, (uint32_t)rd.w, 0ull, last);
+            if (kstep == total - 1)
+                e = res_halfsweep<T, V, 0, true>(sm, J, sd, c, beta, a.seed, (uint32_t)rd.x, (uint32_t)rd.w, 0ull);
+            else
+                res_halfsweep<T, V, 0, false>(sm, J, sd, c, beta, a.seed, (uint32_t)rd.x, (uint32_t)rd.w, 0ull);
             __syncthreads();
         }
     return e;
@@ -124,16 +130,17 @@ __global__ void __launch_bounds__(RES_THREADS, 4) k_resident(DevBatch a, int n_h
         stv<T, VW>(sm + q, v);
     }
     __syncthreads();
-    double e;
-    if (sizeof(T) == 4 && sd.vec == 4) e = res_block<T, (sizeof(T) == 4 ? 4 : 2)>(sm, a, sd, rd, n_hb, nor);
-    else e = res_block<T, 2>(sm, a, sd, rd, n_hb, nor);
+    T e[1];
+    if (sizeof(T) == 4 && sd.vec == 4) e[0] = res_block<T, (sizeof(T) == 4 ? 4 : 2)>(sm, a, sd, rd, n_hb, nor);
+    else e[0] = res_block<T, 2>(sm, a, sd, rd, n_hb, nor);
     for (int q = threadIdx.x * VW; q < n3; q += RES_THREADS * VW) {
         T v[VW];
         ldv<T, VW>(sm + q, v);
         stv<T, VW>(g + q, v);
     }
-    const double H = block_sum(e, red);
-    if (threadIdx.x == 0) a.H[r] = H;
+    double H[1];
+    block_sum_multi<T, 1>(e, H, red);
+    if (threadIdx.x == 0) a.H[r] = H[0];
 }
 
 size_t resident_smem_bytes(int half, bool fp64) { return (size_t)6 * half * (fp64 ? 8 : 4); }
