@@ -18,7 +18,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libpt.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-         "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]
+         "--expt-relaxed-constexpr", "-ftz=true", "-I", os.path.join(ROOT, "include")]
 
 
 def _nvcc() -> str:

@@ -379,17 +379,25 @@ __device__ __forceinline__ void stv(T* __restrict__ p, const T (&o)[V]) {
 // colours; p is the row's checkerboard offset, xs the index of the +-x
 // neighbour that wraps around the row, hy*/hz* the rows' first indices.
 // ---------------------------------------------------------------------------
-template <typename T, int V>
+// J_SHARED: the couplings live in shared memory (plain loads); otherwise in
+// global memory, read through the read-only data cache.
+template <bool J_SHARED, int V>
+__device__ __forceinline__ void ldj(const float* __restrict__ p, float (&o)[V]) {
+    if (J_SHARED) ldv<float, V>(p, o);
+    else ldv_nc<float, V>(p, o);
+}
+
+template <typename T, int V, bool J_SHARED = false>
 __device__ __forceinline__ void nbr_field(const T* __restrict__ oth, const float* __restrict__ Jown,
                                           const float* __restrict__ Joth, int half, int h0, int xs,
                                           int hyp, int hym, int hzp, int hzm, int p, T (&S)[3][V]) {
     {   // +-x: the same row of the other colour, shifted by one (plus xs)
         float jp[V], jm[V];
-        ldv_nc<float, V>(Jown + h0, jp);
+        ldj<J_SHARED, V>(Jown + h0, jp);
         {
             float jx[V];
-            ldv_nc<float, V>(Joth + h0, jx);
-            const float jxs = __ldg(Joth + xs);
+            ldj<J_SHARED, V>(Joth + h0, jx);
+            const float jxs = J_SHARED ? Joth[xs] : __ldg(Joth + xs);
 #pragma unroll
             for (int v = 0; v < V; ++v) jm[v] = p ? jx[v] : (v == 0 ? jxs : jx[v - 1]);
         }
@@ -412,7 +420,7 @@ __device__ __forceinline__ void nbr_field(const T* __restrict__ oth, const float
 #pragma unroll
     for (int dir = 0; dir < 4; ++dir) {
         float jd[V];
-        ldv_nc<float, V>(jsrc[dir], jd);
+        ldj<J_SHARED, V>(jsrc[dir], jd);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             T n[V];

@@ -12,14 +12,15 @@
 // Thread mapping inside a half sweep is the one of the streaming kernel
 // (V = 4 consecutive sites of one row per thread, aligned float4 shared-memory
 // loads, +-x neighbours from the same vector shifted by one plus one wrapped
-// element); couplings come from global memory through the read-only cache
-// (one sample's couplings are shared by all its replicas).
+// element).  The sample's couplings (12 B per site) are staged in shared
+// memory beside the replica, so no half sweep waits on L2: L = 16 takes
+// 48 + 48 KB, two CTAs of 512 threads per SM.
 #include "kernels.h"
 #include "pt_device.cuh"
 
 namespace ptk {
 
-constexpr int RES_THREADS = 256;
+constexpr int RES_THREADS = 512;
 
 // ENERGY (compile time, only the block's last half sweep) also returns the
 // thread's share of H in the spin precision: a few sites per thread, so at
@@ -48,7 +49,7 @@ __device__ __forceinline__ T res_halfsweep(T* __restrict__ sm, const float* __re
         const int hzp = ih0 + hL * (j + L * kp), hzm = ih0 + hL * (j + L * km);
 
         T S[3][V];
-        nbr_field<T, V>(oth, Jown, Joth, half, h0, xs, hyp, hym, hzp, hzm, p, S);
+        nbr_field<T, V, true>(oth, Jown, Joth, half, h0, xs, hyp, hym, hzp, hzm, p, S);
 
         T s[3][V];
         if (KIND == 0) {
@@ -76,13 +77,73 @@ __device__ __forceinline__ T res_halfsweep(T* __restrict__ sm, const float* __re
     return e;
 }
 
+// Row indices of a thread's vector h0 (the same for both colours except the
+// checkerboard offset and the wrapped x neighbour).
+struct VecIdx {
+    int h0, xs0, xs1, hyp, hym, hzp, hzm, p0;
+};
+
+template <int V>
+__device__ __forceinline__ VecIdx vec_idx(const SampleDesc& sd, int h0) {
+    const int hL = sd.hL, L = sd.L;
+    VecIdx q;
+    q.h0 = h0;
+    const int row = (int)fdiv((uint32_t)h0, sd.div_hL);
+    const int ih0 = h0 - row * hL;
+    const int k = (int)fdiv((uint32_t)row, sd.div_L);
+    const int j = row - k * L;
+    q.p0 = (j + k) & 1;
+    const int rb = row * hL;
+    const int left = rb + ((ih0 == 0) ? hL - 1 : ih0 - 1), right = rb + ((ih0 + V == hL) ? 0 : ih0 + V);
+    q.xs0 = q.p0 ? right : left;   // colour 0: p = p0
+    q.xs1 = q.p0 ? left : right;   // colour 1: p = 1 - p0
+    const int jp = (j + 1 == L) ? 0 : j + 1, jm = (j == 0) ? L - 1 : j - 1;
+    const int kp = (k + 1 == L) ? 0 : k + 1, km = (k == 0) ? L - 1 : k - 1;
+    q.hyp = ih0 + hL * (jp + L * k);
+    q.hym = ih0 + hL * (jm + L * k);
+    q.hzp = ih0 + hL * (j + L * kp);
+    q.hzm = ih0 + hL * (j + L * km);
+    return q;
+}
+
+// Overrelaxation half sweep when every thread owns at most one vector of a
+// colour (half <= threads * V): the indices come precomputed.
+template <typename T, int V, bool ENERGY>
+__device__ __forceinline__ T res_or_one(T* __restrict__ sm, const float* __restrict__ J, int half, int color,
+                                        const VecIdx& q) {
+    T e = (T)0;
+    if (q.h0 < half) {
+        T* own = sm + color * 3 * half;
+        const T* oth = sm + (1 - color) * 3 * half;
+        const float* Jown = J + color * 3 * half;
+        const float* Joth = J + (1 - color) * 3 * half;
+        const int p = q.p0 ^ color;
+        const int xs = color ? q.xs1 : q.xs0;
+        T S[3][V];
+        nbr_field<T, V, true>(oth, Jown, Joth, half, q.h0, xs, q.hyp, q.hym, q.hzp, q.hzm, p, S);
+        T s[3][V];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) ldv<T, V>(own + c * half + q.h0, s[c]);
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const V3<T> Sv = {S[0][v], S[1][v], S[2][v]};
+            V3<T> sv = {s[0][v], s[1][v], s[2][v]};
+            or_site(Sv, sv);
+            s[0][v] = sv.x; s[1][v] = sv.y; s[2][v] = sv.z;
+            if (ENERGY) e -= dot(sv, Sv);
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) stv<T, V>(own + c * half + q.h0, s[c]);
+    }
+    return e;
+}
+
 // The sweep block of one replica (the CTA's replica is held in `sm`).  Heat-
 // bath half sweeps (1 of 1 + 5L/4 sweeps) run one site per thread so that the
 // register peak is set by the vectorised overrelaxation path.
 template <typename T, int V>
-__device__ __forceinline__ T res_block(T* sm, const DevBatch& a, const SampleDesc& sd, const int4& rd, int n_hb,
-                                       int n_or) {
-    const float* J = a.J + sd.J_off;
+__device__ __forceinline__ T res_block(T* sm, const float* J, const DevBatch& a, const SampleDesc& sd,
+                                       const int4& rd, int n_hb, int n_or) {
     const T beta = (T)a.betas[sd.beta_off + rd.z];
     const unsigned long long step0 = *a.d_step;
     const int total = 2 * (n_hb + n_or);
@@ -97,6 +158,16 @@ __device__ __forceinline__ T res_block(T* sm, const DevBatch& a, const SampleDes
                 res_halfsweep<T, 1, 1, false>(sm, J, sd, c, beta, a.seed, (uint32_t)rd.x, (uint32_t)rd.w, st);
             __syncthreads();
         }
+    if (sd.half <= RES_THREADS * V) {
+        const VecIdx q = vec_idx<V>(sd, (int)threadIdx.x * V);
+        for (int o = 0; o < n_or; ++o)
+            for (int c = 0; c < 2; ++c, ++kstep) {
+                if (kstep == total - 1) e = res_or_one<T, V, true>(sm, J, sd.half, c, q);
+                else res_or_one<T, V, false>(sm, J, sd.half, c, q);
+                __syncthreads();
+            }
+        return e;
+    }
     for (int o = 0; o < n_or; ++o)
         for (int c = 0; c < 2; ++c, ++kstep) {
             if (kstep == total - 1)
@@ -112,7 +183,7 @@ __device__ __forceinline__ T res_block(T* sm, const DevBatch& a, const SampleDes
 // width decides the vector width (4 or 2 sites per thread in float, 2 in
 // double); the overrelaxation count is per sample when a.nor_s is given.
 template <typename T>
-__global__ void __launch_bounds__(RES_THREADS, 4) k_resident(DevBatch a, int n_hb, int n_or) {
+__global__ void __launch_bounds__(RES_THREADS, 2) k_resident(DevBatch a, int n_hb, int n_or) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw);
     __shared__ double red[32];
@@ -129,10 +200,18 @@ __global__ void __launch_bounds__(RES_THREADS, 4) k_resident(DevBatch a, int n_h
         ldv<T, VW>(g + q, v);
         stv<T, VW>(sm + q, v);
     }
+    // couplings after the spins (6 half floats; n3 * sizeof(T) is a multiple of 16 B)
+    float* sJ = reinterpret_cast<float*>(sm + n3);
+    const float* gJ = a.J + sd.J_off;
+    for (int q = threadIdx.x * 4; q < n3; q += RES_THREADS * 4) {
+        float v[4];
+        ldv_nc<float, 4>(gJ + q, v);
+        stv<float, 4>(sJ + q, v);
+    }
     __syncthreads();
     T e[1];
-    if (sizeof(T) == 4 && sd.vec == 4) e[0] = res_block<T, (sizeof(T) == 4 ? 4 : 2)>(sm, a, sd, rd, n_hb, nor);
-    else e[0] = res_block<T, 2>(sm, a, sd, rd, n_hb, nor);
+    if (sizeof(T) == 4 && sd.vec == 4) e[0] = res_block<T, (sizeof(T) == 4 ? 4 : 2)>(sm, sJ, a, sd, rd, n_hb, nor);
+    else e[0] = res_block<T, 2>(sm, sJ, a, sd, rd, n_hb, nor);
     for (int q = threadIdx.x * VW; q < n3; q += RES_THREADS * VW) {
         T v[VW];
         ldv<T, VW>(sm + q, v);
@@ -143,14 +222,18 @@ __global__ void __launch_bounds__(RES_THREADS, 4) k_resident(DevBatch a, int n_h
     if (threadIdx.x == 0) a.H[r] = H[0];
 }
 
-size_t resident_smem_bytes(int half, bool fp64) { return (size_t)6 * half * (fp64 ? 8 : 4); }
+// One replica (6 half elements of T) and its sample's couplings (6 half floats).
+size_t resident_smem_bytes(int half, bool fp64) { return (size_t)6 * half * ((fp64 ? 8 : 4) + 4); }
 
 bool resident_supported(const SampleDesc& sd, bool fp64, int vec) {
-    // 16- or 8-byte rows (vec 4 or 2; double only 2) and at most 100 KB of
-    // spins per CTA (two CTAs per SM)
+    // 16- or 8-byte rows (vec 4 or 2; double only 2), 16-byte aligned
+    // coupling blocks (6 half a multiple of 4), and at most 200 KB per CTA
+    // (two CTAs per SM up to 112 KB, e.g. L = 16 in float; one above, e.g.
+    // L = 16 in double, where the autotuner weighs it against streaming)
     if (vec != 4 && vec != 2) return false;
     if (fp64 && vec != 2) return false;
-    return sd.hL % vec == 0 && resident_smem_bytes(sd.half, fp64) <= 100 * 1024;
+    if ((6 * sd.half) % 4 != 0) return false;
+    return sd.hL % vec == 0 && resident_smem_bytes(sd.half, fp64) <= 200 * 1024;
 }
 
 cudaError_t launch_resident(const DevBatch& b, bool fp64, int n_hb, int n_or, cudaStream_t st) {
