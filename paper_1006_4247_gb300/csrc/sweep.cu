@@ -31,7 +31,7 @@ __global__ void __launch_bounds__(TILE) k_sweep(DevBatch a, const int* __restric
     const SampleDesc& sd = a.samples[rd.x];
     const int half = sd.half, hL = sd.hL, L = sd.L;
     const int h0 = tl.y + (int)threadIdx.x * V;
-    double e = 0.0;
+    T e[1] = {(T)0};  // this thread's V sites of H (energy launches)
     if (h0 < half) {
         T* base = (T*)a.spins + a.chain_off[rd.y] + (long long)a.bufmap[tl.x] * (6LL * half);
         T* own = base + color * 3 * half;
@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(TILE) k_sweep(DevBatch a, const int* __restric
                 if (KIND == 0) or_site(Sv, sv);
             }
             s[0][v] = sv.x; s[1][v] = sv.y; s[2][v] = sv.z;
-            if (ENERGY || KIND == 2) e -= (double)dot(sv, Sv);
+            if (ENERGY || KIND == 2) e[0] -= dot(sv, Sv);
         }
         if (KIND != 2) {
 #pragma unroll
@@ -82,8 +82,9 @@ __global__ void __launch_bounds__(TILE) k_sweep(DevBatch a, const int* __restric
         }
     }
     if (ENERGY || KIND == 2) {
-        const double tot = block_sum(e, sh);
-        if (threadIdx.x == 0) a.part[t] = tot;
+        double tot[1];
+        block_sum_multi<T, 1>(e, tot, sh);
+        if (threadIdx.x == 0) a.part[t] = tot[0];
     }
 }
 
@@ -133,12 +134,13 @@ __global__ void k_advance_step(unsigned long long* d_step, int by) { *d_step += 
 
 // Overlap Q_ab = sum_x s0_a,x s1_b,x between copy 0 and copy 1 at the same
 // beta index (Eq. over) and chi = (1/N) sum_ab Q_ab^2.  One block per
-// (sample, beta index); each thread accumulates its sites in T in chunks of
-// at most 32 sites, then in double; warp shuffles and one shared-memory pass
-// finish the nine sums in a fixed order.
+// (sample, beta index); each thread reads 16-byte vectors of consecutive sites
+// (a vector never straddles the two colours: half is a multiple of 4) and
+// accumulates them in T in chunks of at most 32 sites, then in double; warp
+// shuffles and one shared-memory pass finish the nine sums in a fixed order.
 template <typename T>
 __global__ void __launch_bounds__(TILE) k_overlap(DevBatch a) {
-    __shared__ double sh[9][TILE / 32];
+    __shared__ double sh[9 * 32];
     const int q = blockIdx.x;  // beta_off(s) + b over all samples
     const int s = a.q_sample[q];
     const SampleDesc& sd = a.samples[s];
@@ -150,43 +152,49 @@ __global__ void __launch_bounds__(TILE) k_overlap(DevBatch a) {
     double acc[9];
 #pragma unroll
     for (int n = 0; n < 9; ++n) acc[n] = 0.0;
-    const int N = 2 * half;
-    for (int base = 0; base < N; base += 32 * TILE) {
+    constexpr int V = 16 / sizeof(T);
+    constexpr int CH = 32 / V;  // vectors per chunk of 32 sites
+    const int N = 2 * half, NV = N / V;
+    for (int base = 0; base < NV; base += CH * TILE) {
         T part[9];
 #pragma unroll
         for (int n = 0; n < 9; ++n) part[n] = (T)0;
-        const int end = min(N, base + 32 * TILE);
-        for (int x = base + (int)threadIdx.x; x < end; x += TILE) {
+        const int end = min(NV, base + CH * TILE);
+        for (int xv = base + (int)threadIdx.x; xv < end; xv += TILE) {
+            const int x = xv * V;
             const int c = x >= half ? 1 : 0;
             const int h = x - c * half;
             const T* p0 = b0 + c * 3 * half + h;
             const T* p1 = b1 + c * 3 * half + h;
-            const T u0[3] = {p0[0], p0[half], p0[2 * half]};
-            const T u1[3] = {p1[0], p1[half], p1[2 * half]};
+            T u0[3][V], u1[3][V];
 #pragma unroll
-            for (int n = 0; n < 9; ++n) part[n] += u0[n / 3] * u1[n % 3];
+            for (int k = 0; k < 3; ++k) {
+                ldv_nc<T, V>(p0 + k * half, u0[k]);
+                ldv_nc<T, V>(p1 + k * half, u1[k]);
+            }
+#pragma unroll
+            for (int n = 0; n < 9; ++n)
+#pragma unroll
+                for (int v = 0; v < V; ++v) part[n] += u0[n / 3][v] * u1[n % 3][v];
         }
 #pragma unroll
         for (int n = 0; n < 9; ++n) acc[n] += (double)part[n];
     }
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    // the thread totals (double over chunks) enter the warp tree in T, the
+    // warp sums are added in double (the precision policy of all reductions)
+    T tp[9];
 #pragma unroll
-    for (int n = 0; n < 9; ++n) {
-        const double v = warp_sum(acc[n]);
-        if (lane == 0) sh[n][wid] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < 32) {
+    for (int n = 0; n < 9; ++n) tp[n] = (T)acc[n];
+    double tot[9];
+    block_sum_multi<T, 9>(tp, tot, sh);
+    if (threadIdx.x == 0) {
         double chi = 0.0;
+#pragma unroll
         for (int n = 0; n < 9; ++n) {
-            double v = (lane < TILE / 32) ? sh[n][lane] : 0.0;
-            v = warp_sum(v);
-            if (lane == 0) {
-                a.Q[(long long)q * 9 + n] = v;
-                chi += v * v;
-            }
+            a.Q[(long long)q * 9 + n] = tot[n];
+            chi += tot[n] * tot[n];
         }
-        if (lane == 0) a.chi[q] = chi / (double)N;
+        a.chi[q] = chi / (double)N;
     }
 }
 
