@@ -269,7 +269,7 @@ def ours(args):
     nor_samples = None if len(set(nor)) == 1 else nor
     tune = None
     if args.policy == "auto" and not args.no_autotune:
-        tune = eng.autotune(w.n_hb, min(max(min(nor), 1), 4))
+        tune = eng.autotune(w.n_hb, max(nor))  # the block as the cycle runs it
     else:
         eng.set_policy(args.policy)
 
@@ -360,7 +360,7 @@ def ours(args):
         return {"bound": "alu", "achieved": upd * 60.0 / t / 1e12, "peak": peak_alu / 1e12, "unit": "TFLOP/s",
                 "frac": upd * 60.0 / t / peak_alu,
                 "traffic": ncu_traffic("k_resident", w.name, args.precision) if uniform else None,
-                "kernel": "k_resident (sweep block in shared memory)",
+                "kernel": "k_resident / k_resident_cl (sweep block in shared memory, one CTA or a cluster)",
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz",
                 "alg_flops_per_launch": upd * 60.0 / n_launch, "avg_launch_us": t / n_launch * 1e6,
                 "effective_hbm_GBps": upd * 36.4 / t / 1e9}

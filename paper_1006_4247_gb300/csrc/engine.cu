@@ -283,14 +283,14 @@ void choose_paths(pt_engine* e) {
         SampleDesc& sd = e->samples[s];
         const int def_vec = vec_width(sd.hL, e->fp64);
         const int vec = (!e->tuned_vec.empty() && e->tuned_vec[s] > 0) ? e->tuned_vec[s] : def_vec;
-        const bool fits = resident_supported(sd, e->fp64, vec) || resident_supported(sd, e->fp64, def_vec);
+        const bool fits = resident_cluster(sd, e->fp64, vec) > 0 || resident_cluster(sd, e->fp64, def_vec) > 0;
         e->all_resident = e->all_resident && fits;
         bool res;
         if (e->policy == PT_POLICY_STREAMING) res = false;
         else if (e->policy == PT_POLICY_RESIDENT) res = fits;
         else res = (!e->tuned_res.empty() && e->tuned_res[s] >= 0) ? (e->tuned_res[s] == 1 && fits) : fits;
-        sd.resident = res ? 1 : 0;
-        sd.vec = res ? (resident_supported(sd, e->fp64, vec) ? vec : def_vec) : vec;
+        sd.vec = res ? (resident_cluster(sd, e->fp64, vec) > 0 ? vec : def_vec) : vec;
+        sd.resident = res ? resident_cluster(sd, e->fp64, sd.vec) : 0;  // CTAs per replica
         sd.tiles_per_rep = (sd.half + TILE * sd.vec - 1) / (TILE * sd.vec);
     }
 }
@@ -329,16 +329,21 @@ pt_status rebuild_lists(pt_engine* e) {
         }
         d.sclass_count[cls] = (int)e->stile_idx.size() - d.sclass_begin[cls];
     }
-    d.res_max_half = 0;
     e->any_streaming = false;
-    for (const SampleDesc& sd : e->samples) {
-        if (sd.resident) {
+    for (const SampleDesc& sd : e->samples)
+        if (!sd.resident) e->any_streaming = true;
+    // resident replicas grouped by CTAs per replica (1, 2, 4, 8)
+    for (int g = 0; g < 4; ++g) {
+        d.rcl_begin[g] = (int)e->res_reps.size();
+        d.rcl_half[g] = 0;
+        for (const SampleDesc& sd : e->samples) {
+            if (sd.resident != (1 << g)) continue;
             for (int q = 0; q < e->C * sd.NT; ++q) e->res_reps.push_back(sd.r0 + q);
-            d.res_max_half = std::max(d.res_max_half, sd.half);
-        } else {
-            e->any_streaming = true;
+            d.rcl_half[g] = std::max(d.rcl_half[g], sd.half);
         }
+        d.rcl_count[g] = (int)e->res_reps.size() - d.rcl_begin[g];
     }
+    d.res_max_half = d.rcl_half[0];
     if ((size_t)t > e->tile_cap) return fail(PT_ERR_STATE, "tile list exceeds its capacity");
     // every sample streaming: the subset is the whole list, index it directly
     d.stiles = e->res_reps.empty() ? nullptr : e->d_stiles;
@@ -707,7 +712,7 @@ static pt_status sweep_impl(pt_engine* e, int n_hb, int n_or, const int* nor) {
     }
     const bool fuse = (nor == nullptr);  // per-sample counts: energies after the block
     if (!e->res_reps.empty())
-        RUN(PT_KERNEL_RESIDENT, 1, launch_resident(e->d, e->fp64, n_hb, n_or, e->stream));
+        RUN(PT_KERNEL_RESIDENT, resident_launch_count(e->d), launch_resident(e->d, e->fp64, n_hb, n_or, e->stream));
     if (e->any_streaming) {
         const int nl = sweep_stream_launch_count(e->d);
         const bool tma = e->all_tma && e->res_reps.empty() && nor == nullptr;
@@ -906,7 +911,7 @@ pt_status pt_autotune(pt_handle e, int n_hb, int n_or, int* choice, double* best
                 if (res) {
                     bool ok = true;
                     for (const SampleDesc& sd : e->samples)
-                        if (sd.L == L && !resident_supported(sd, e->fp64, vec)) ok = false;
+                        if (sd.L == L && resident_cluster(sd, e->fp64, vec) == 0) ok = false;
                     if (!ok) continue;
                 }
                 cand.push_back({res, vec});

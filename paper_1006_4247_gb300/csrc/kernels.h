@@ -55,6 +55,9 @@ struct DevBatch {
     // streaming subset is grouped the same way inside stiles
     int vclass_begin[3], vclass_count[3], vclass_width[3];
     int sclass_begin[3], sclass_count[3];
+    // resident replicas grouped by CTAs per replica (1, 2, 4, 8): slices of
+    // res_reps and the largest L^3/2 of each group
+    int rcl_begin[4], rcl_count[4], rcl_half[4];
 };
 
 // Record the text returned by pt_last_error() for the calling thread.
@@ -95,6 +98,12 @@ cudaError_t launch_or_tma(const DevBatch& b, int color, cudaStream_t st);
 // Resident sweep blocks: one CTA per replica runs n_hb + n_or sweeps in shared
 // memory and writes H[r].
 bool resident_supported(const SampleDesc& sd, bool fp64, int vec);
+// CTAs that hold one replica of the sample on chip: 1 when one CTA can
+// (resident_supported), else the smallest cluster of 2, 4 or 8 CTAs that can
+// (each CTA a slab of L/size z planes), 0 when none can.
+int resident_cluster(const SampleDesc& sd, bool fp64, int vec);
+// Kernels one resident block launches (one per non-empty group).
+int resident_launch_count(const DevBatch& b);
 cudaError_t launch_resident(const DevBatch& b, bool fp64, int n_hb, int n_or, cudaStream_t st);
 
 }  // namespace ptk

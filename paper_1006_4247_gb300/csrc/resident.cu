@@ -15,8 +15,12 @@
 // element).  The sample's couplings (12 B per site) are staged in shared
 // memory beside the replica, so no half sweep waits on L2: L = 16 takes
 // 48 + 48 KB, two CTAs of 512 threads per SM.
+#include <cooperative_groups.h>
+
 #include "kernels.h"
 #include "pt_device.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace ptk {
 
@@ -187,7 +191,7 @@ __global__ void __launch_bounds__(RES_THREADS, 2) k_resident(DevBatch a, int n_h
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw);
     __shared__ double red[32];
-    const int r = a.res_reps[blockIdx.x];
+    const int r = a.res_reps[a.rcl_begin[0] + (int)blockIdx.x];
     const int4 rd = a.reps[r];
     const SampleDesc& sd = a.samples[rd.x];
     const int half = sd.half;
@@ -222,6 +226,308 @@ __global__ void __launch_bounds__(RES_THREADS, 2) k_resident(DevBatch a, int n_h
     if (threadIdx.x == 0) a.H[r] = H[0];
 }
 
+// ---------------------------------------------------------------------------
+// Cluster-resident block: a replica too large for one SM (L = 24, 32 in
+// float) is split over a cluster of CS CTAs, CTA `rank` holding the z planes
+// [rank Lz, (rank + 1) Lz), Lz = L / CS, of both colours and their
+// couplings in shared memory ([colour][component][hl], hl = half / CS, the
+// same layout as the global colour-split arrays restricted to the slab).
+// Neighbours in the planes just outside the slab are read from the adjacent
+// CTAs' shared memory (distributed shared memory); a cluster barrier
+// separates the half sweeps.  Every CTA executes the same sequence of
+// barriers, so no CTA waits on a condition only another one can change.
+// ---------------------------------------------------------------------------
+constexpr int CL_THREADS = 1024;
+
+// Neighbour field of V sites of a slab row; the z+ row may live in the next
+// CTA (othP) and the z- row with its couplings in the previous one (othM,
+// JothM); all pointers address [component][hl] arrays of the other colour.
+template <typename T, int V>
+__device__ __forceinline__ void nbr_field_cl(const T* oth, const float* Jown, const float* Joth, int hl, int h0,
+                                             int xs, int hyp, int hym, const T* othP, int hzp, const T* othM,
+                                             const float* JothM, int hzm, int p, T (&S)[3][V]) {
+    {   // +-x: the same row of the other colour, shifted by one (plus xs)
+        float jp[V], jm[V];
+        ldv<float, V>(Jown + h0, jp);
+        {
+            float jx[V];
+            ldv<float, V>(Joth + h0, jx);
+            const float jxs = Joth[xs];
+#pragma unroll
+            for (int v = 0; v < V; ++v) jm[v] = p ? jx[v] : (v == 0 ? jxs : jx[v - 1]);
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const T* o = oth + c * hl;
+            T O[V];
+            ldv<T, V>(o + h0, O);
+            const T os = o[xs];
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const T xp = p ? (v == V - 1 ? os : O[v + 1]) : O[v];
+                const T xm = p ? O[v] : (v == 0 ? os : O[v - 1]);
+                S[c][v] = (T)jp[v] * xp + (T)jm[v] * xm;
+            }
+        }
+    }
+    const float* jsrc[4] = {Jown + hl + h0, Joth + hl + hym, Jown + 2 * hl + h0, JothM + 2 * hl + hzm};
+    const T* nsrc[4] = {oth + hyp, oth + hym, othP + hzp, othM + hzm};
+#pragma unroll
+    for (int dir = 0; dir < 4; ++dir) {
+        float jd[V];
+        ldv<float, V>(jsrc[dir], jd);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            T n[V];
+            ldv<T, V>(nsrc[dir] + c * hl, n);
+#pragma unroll
+            for (int v = 0; v < V; ++v) S[c][v] += (T)jd[v] * n[v];
+        }
+    }
+}
+
+struct Slab {
+    int hl, Lz, k0, rank, cs;  // sites per colour, planes, first plane, CTA rank, cluster size
+};
+
+template <typename T, int V, int KIND, bool ENERGY>
+__device__ __forceinline__ T cl_halfsweep(cg::cluster_group& cl, T* __restrict__ sm, const float* __restrict__ J,
+                                          const SampleDesc& sd, const Slab& sb, int color, T beta,
+                                          unsigned long long seed, uint32_t sample, uint32_t rep_id,
+                                          unsigned long long step) {
+    const int hl = sb.hl, hL = sd.hL, L = sd.L;
+    T* own = sm + color * 3 * hl;
+    const T* oth = sm + (1 - color) * 3 * hl;
+    const float* Jown = J + color * 3 * hl;
+    const float* Joth = J + (1 - color) * 3 * hl;
+    T e = (T)0;
+    for (int h0 = (int)threadIdx.x * V; h0 < hl; h0 += CL_THREADS * V) {
+        const int row = (int)fdiv((uint32_t)h0, sd.div_hL);  // slab row j + L kl
+        const int ih0 = h0 - row * hL;
+        const int kl = (int)fdiv((uint32_t)row, sd.div_L);
+        const int j = row - kl * L;
+        const int p = (j + sb.k0 + kl + color) & 1;
+        const int rb = row * hL;
+        const int xs = p ? rb + ((ih0 + V == hL) ? 0 : ih0 + V) : rb + ((ih0 == 0) ? hL - 1 : ih0 - 1);
+        const int jp = (j + 1 == L) ? 0 : j + 1, jm = (j == 0) ? L - 1 : j - 1;
+        const int hyp = ih0 + hL * (jp + L * kl), hym = ih0 + hL * (jm + L * kl);
+        const bool topz = kl + 1 == sb.Lz, botz = kl == 0;  // uniform over a warp (one plane)
+        const T* othP = oth;
+        if (topz) othP = cl.map_shared_rank(const_cast<T*>(oth), sb.rank + 1 == sb.cs ? 0 : sb.rank + 1);
+        const int hzp = ih0 + hL * (j + L * (topz ? 0 : kl + 1));
+        const T* othM = oth;
+        const float* JothM = Joth;
+        if (botz) {
+            const int rm = sb.rank == 0 ? sb.cs - 1 : sb.rank - 1;
+            othM = cl.map_shared_rank(const_cast<T*>(oth), rm);
+            JothM = cl.map_shared_rank(const_cast<float*>(Joth), rm);
+        }
+        const int hzm = ih0 + hL * (j + L * (botz ? sb.Lz - 1 : kl - 1));
+
+        T S[3][V];
+        nbr_field_cl<T, V>(oth, Jown, Joth, hl, h0, xs, hyp, hym, othP, hzp, othM, JothM, hzm, p, S);
+        T s[3][V];
+        if (KIND == 0) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) ldv<T, V>(own + c * hl + h0, s[c]);
+        }
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const V3<T> Sv = {S[0][v], S[1][v], S[2][v]};
+            V3<T> sv;
+            if (KIND == 1) {
+                const int x = 2 * (ih0 + v) + p + L * (row + L * sb.k0);
+                const uint4 w = rng_words(seed, sample, (uint32_t)x, rep_id, step, 0u);
+                sv = hb_site<T>(beta, Sv, w.x, w.y);
+            } else {
+                sv = {s[0][v], s[1][v], s[2][v]};
+                or_site(Sv, sv);
+            }
+            s[0][v] = sv.x; s[1][v] = sv.y; s[2][v] = sv.z;
+            if (ENERGY) e -= dot(sv, Sv);
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) stv<T, V>(own + c * hl + h0, s[c]);
+    }
+    return e;
+}
+
+// Indices of a thread's slab vector, computed once per launch when every
+// thread owns at most one vector of a colour (hl <= threads * V).
+struct VecIdxCl {
+    int h0, xs0, xs1, hyp, hym, hzp, hzm, pz;  // pz: bit 0 p of colour 0, bit 1 z+ remote, bit 2 z- remote
+};
+
+template <int V>
+__device__ __forceinline__ VecIdxCl vec_idx_cl(const SampleDesc& sd, const Slab& sb, int h0) {
+    const int hL = sd.hL, L = sd.L;
+    VecIdxCl q;
+    q.h0 = h0;
+    const int row = (int)fdiv((uint32_t)h0, sd.div_hL);
+    const int ih0 = h0 - row * hL;
+    const int kl = (int)fdiv((uint32_t)row, sd.div_L);
+    const int j = row - kl * L;
+    const int p0 = (j + sb.k0 + kl) & 1;
+    const int rb = row * hL;
+    const int left = rb + ((ih0 == 0) ? hL - 1 : ih0 - 1), right = rb + ((ih0 + V == hL) ? 0 : ih0 + V);
+    q.xs0 = p0 ? right : left;
+    q.xs1 = p0 ? left : right;
+    const int jp = (j + 1 == L) ? 0 : j + 1, jm = (j == 0) ? L - 1 : j - 1;
+    q.hyp = ih0 + hL * (jp + L * kl);
+    q.hym = ih0 + hL * (jm + L * kl);
+    const bool topz = kl + 1 == sb.Lz, botz = kl == 0;
+    q.hzp = ih0 + hL * (j + L * (topz ? 0 : kl + 1));
+    q.hzm = ih0 + hL * (j + L * (botz ? sb.Lz - 1 : kl - 1));
+    q.pz = p0 | (topz ? 2 : 0) | (botz ? 4 : 0);
+    return q;
+}
+
+// Overrelaxation half sweep of the slab with precomputed indices; the
+// neighbour CTAs' arrays are mapped only by the warps of the boundary planes
+// (a warp's vectors lie in one plane, so the branch is uniform).
+template <typename T, int V, bool ENERGY>
+__device__ __forceinline__ T cl_or_one(cg::cluster_group& cl, T* __restrict__ sm, const float* __restrict__ J,
+                                       int hl, int rank, int cs, int color, const VecIdxCl& q) {
+    T e = (T)0;
+    if (q.h0 < hl) {
+        T* own = sm + color * 3 * hl;
+        const T* oth = sm + (1 - color) * 3 * hl;
+        const float* Jown = J + color * 3 * hl;
+        const float* Joth = J + (1 - color) * 3 * hl;
+        const int p = (q.pz & 1) ^ color;
+        const int xs = color ? q.xs1 : q.xs0;
+        const T* othP = oth;
+        if (q.pz & 2) othP = cl.map_shared_rank(const_cast<T*>(oth), rank + 1 == cs ? 0 : rank + 1);
+        const T* othM = oth;
+        const float* JothM = Joth;
+        if (q.pz & 4) {
+            const int rm = rank == 0 ? cs - 1 : rank - 1;
+            othM = cl.map_shared_rank(const_cast<T*>(oth), rm);
+            JothM = cl.map_shared_rank(const_cast<float*>(Joth), rm);
+        }
+        T S[3][V];
+        nbr_field_cl<T, V>(oth, Jown, Joth, hl, q.h0, xs, q.hyp, q.hym, othP, q.hzp, othM, JothM, q.hzm, p, S);
+        T s[3][V];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) ldv<T, V>(own + c * hl + q.h0, s[c]);
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const V3<T> Sv = {S[0][v], S[1][v], S[2][v]};
+            V3<T> sv = {s[0][v], s[1][v], s[2][v]};
+            or_site(Sv, sv);
+            s[0][v] = sv.x; s[1][v] = sv.y; s[2][v] = sv.z;
+            if (ENERGY) e -= dot(sv, Sv);
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) stv<T, V>(own + c * hl + q.h0, s[c]);
+    }
+    return e;
+}
+
+template <typename T, int V>
+__device__ __forceinline__ T cl_block(cg::cluster_group& cl, T* sm, const float* J, const DevBatch& a,
+                                      const SampleDesc& sd, const Slab& sb, const int4& rd, int n_hb, int n_or) {
+    const T beta = (T)a.betas[sd.beta_off + rd.z];
+    const unsigned long long step0 = *a.d_step;
+    const int total = 2 * (n_hb + n_or);
+    T e = (T)0;
+    int kstep = 0;
+    for (int hb = 0; hb < n_hb; ++hb)
+        for (int c = 0; c < 2; ++c, ++kstep) {
+            const unsigned long long st = step0 + (unsigned long long)kstep;
+            if (kstep == total - 1)
+                e = cl_halfsweep<T, 1, 1, true>(cl, sm, J, sd, sb, c, beta, a.seed, (uint32_t)rd.x, (uint32_t)rd.w,
+                                                st);
+            else
+                cl_halfsweep<T, 1, 1, false>(cl, sm, J, sd, sb, c, beta, a.seed, (uint32_t)rd.x, (uint32_t)rd.w,
+                                             st);
+            cl.sync();
+        }
+    if (sb.hl <= CL_THREADS * V) {
+        const VecIdxCl q = vec_idx_cl<V>(sd, sb, (int)threadIdx.x * V);
+        for (int o = 0; o < n_or; ++o)
+            for (int c = 0; c < 2; ++c, ++kstep) {
+                if (kstep == total - 1) e = cl_or_one<T, V, true>(cl, sm, J, sb.hl, sb.rank, sb.cs, c, q);
+                else cl_or_one<T, V, false>(cl, sm, J, sb.hl, sb.rank, sb.cs, c, q);
+                cl.sync();
+            }
+        return e;
+    }
+    for (int o = 0; o < n_or; ++o)
+        for (int c = 0; c < 2; ++c, ++kstep) {
+            if (kstep == total - 1)
+                e = cl_halfsweep<T, V, 0, true>(cl, sm, J, sd, sb, c, beta, a.seed, (uint32_t)rd.x, (uint32_t)rd.w,
+                                                0ull);
+            else
+                cl_halfsweep<T, V, 0, false>(cl, sm, J, sd, sb, c, beta, a.seed, (uint32_t)rd.x, (uint32_t)rd.w,
+                                             0ull);
+            cl.sync();
+        }
+    return e;
+}
+
+// One cluster per replica of the group that starts at res_reps[begin].
+template <typename T>
+__global__ void __launch_bounds__(CL_THREADS, 1) k_resident_cl(DevBatch a, int n_hb, int n_or, int begin) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[32];
+    __shared__ double cta_total;
+    cg::cluster_group cl = cg::this_cluster();
+    const int cs = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+    const int r = a.res_reps[begin + (int)blockIdx.x / cs];
+    const int4 rd = a.reps[r];
+    const SampleDesc& sd = a.samples[rd.x];
+    const int half = sd.half;
+    Slab sb;
+    sb.hl = half / cs;
+    sb.Lz = sd.L / cs;
+    sb.k0 = rank * sb.Lz;
+    sb.rank = rank;
+    sb.cs = cs;
+    const int hl = sb.hl, n3 = 6 * hl;
+    T* sm = reinterpret_cast<T*>(smem_raw);
+    float* sJ = reinterpret_cast<float*>(sm + n3);  // n3 * sizeof(T) is a multiple of 16 B
+    const int nor = a.nor_s ? a.nor_s[rd.x] : n_or;
+    // this CTA's slab: 6 contiguous runs of hl elements (colour, component)
+    const T* g = (const T*)a.spins + a.chain_off[rd.y] + (long long)a.bufmap[r] * (6LL * half);
+    const float* gJ = a.J + sd.J_off;
+    constexpr int VW = 16 / sizeof(T);
+    for (int q = threadIdx.x * VW; q < n3; q += CL_THREADS * VW) {
+        const int run = q / hl, off = q - run * hl;  // hl is a multiple of VW
+        T v[VW];
+        ldv<T, VW>(g + (long long)run * half + rank * hl + off, v);
+        stv<T, VW>(sm + q, v);
+    }
+    for (int q = threadIdx.x * 4; q < n3; q += CL_THREADS * 4) {
+        const int run = q / hl, off = q - run * hl;
+        float v[4];
+        ldv_nc<float, 4>(gJ + (long long)run * half + rank * hl + off, v);
+        stv<float, 4>(sJ + q, v);
+    }
+    cl.sync();  // every slab loaded before any neighbour reads it
+    T e[1];
+    if (sizeof(T) == 4 && sd.vec == 4) e[0] = cl_block<T, (sizeof(T) == 4 ? 4 : 2)>(cl, sm, sJ, a, sd, sb, rd, n_hb, nor);
+    else e[0] = cl_block<T, 2>(cl, sm, sJ, a, sd, sb, rd, n_hb, nor);
+    // the last barrier of the block has passed: the slab is final
+    T* gw = (T*)a.spins + a.chain_off[rd.y] + (long long)a.bufmap[r] * (6LL * half);
+    for (int q = threadIdx.x * VW; q < n3; q += CL_THREADS * VW) {
+        const int run = q / hl, off = q - run * hl;
+        T v[VW];
+        ldv<T, VW>(sm + q, v);
+        stv<T, VW>(gw + (long long)run * half + rank * hl + off, v);
+    }
+    double tot[1];
+    block_sum_multi<T, 1>(e, tot, red);
+    if (threadIdx.x == 0) cta_total = tot[0];
+    cl.sync();
+    if (rank == 0 && threadIdx.x == 0) {
+        double H = 0.0;
+        for (int q = 0; q < cs; ++q) H += *cl.map_shared_rank(&cta_total, q);
+        a.H[r] = H;
+    }
+    cl.sync();  // no CTA leaves while rank 0 reads its total
+}
+
 // One replica (6 half elements of T) and its sample's couplings (6 half floats).
 size_t resident_smem_bytes(int half, bool fp64) { return (size_t)6 * half * ((fp64 ? 8 : 4) + 4); }
 
@@ -236,20 +542,69 @@ bool resident_supported(const SampleDesc& sd, bool fp64, int vec) {
     return sd.hL % vec == 0 && resident_smem_bytes(sd.half, fp64) <= 200 * 1024;
 }
 
-cudaError_t launch_resident(const DevBatch& b, bool fp64, int n_hb, int n_or, cudaStream_t st) {
-    if (b.n_res_reps == 0) return cudaSuccess;
-    const size_t smem = resident_smem_bytes(b.res_max_half, fp64);
-    cudaError_t e;
-    if (fp64) {
-        e = ensure_smem((const void*)k_resident<double>, smem);
-        if (e != cudaSuccess) return e;
-        k_resident<double><<<b.n_res_reps, RES_THREADS, smem, st>>>(b, n_hb, n_or);
-    } else {
-        e = ensure_smem((const void*)k_resident<float>, smem);
-        if (e != cudaSuccess) return e;
-        k_resident<float><<<b.n_res_reps, RES_THREADS, smem, st>>>(b, n_hb, n_or);
+int resident_cluster(const SampleDesc& sd, bool fp64, int vec) {
+    if (resident_supported(sd, fp64, vec)) return 1;
+    if (vec != 4 && vec != 2) return 0;
+    if (fp64 && vec != 2) return 0;
+    if (sd.hL % vec) return 0;
+    for (int cs : {2, 4, 8}) {
+        if (sd.L % cs) continue;
+        const int hl = sd.half / cs;  // hL L (L / cs) sites: a multiple of vec
+        if (hl % 4 != 0) continue;    // 16-byte aligned runs for the slab copies
+        if (resident_smem_bytes(hl, fp64) <= 200 * 1024) return cs;
     }
-    return cudaGetLastError();
+    return 0;
+}
+
+int resident_launch_count(const DevBatch& b) {
+    int n = 0;
+    for (int g = 0; g < 4; ++g) n += b.rcl_count[g] > 0;
+    return n;
+}
+
+template <typename T>
+static cudaError_t launch_cl(const DevBatch& b, int g, int n_hb, int n_or, cudaStream_t st) {
+    const int cs = 1 << g;
+    const size_t smem = resident_smem_bytes(b.rcl_half[g] / cs, sizeof(T) == 8);
+    cudaError_t e = ensure_smem((const void*)k_resident_cl<T>, smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(b.rcl_count[g] * cs), 1, 1);
+    cfg.blockDim = dim3(CL_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_resident_cl<T>, b, n_hb, n_or, b.rcl_begin[g]);
+}
+
+cudaError_t launch_resident(const DevBatch& b, bool fp64, int n_hb, int n_or, cudaStream_t st) {
+    cudaError_t e = cudaSuccess;
+    if (b.rcl_count[0] > 0) {
+        const size_t smem = resident_smem_bytes(b.rcl_half[0], fp64);
+        if (fp64) {
+            e = ensure_smem((const void*)k_resident<double>, smem);
+            if (e != cudaSuccess) return e;
+            k_resident<double><<<b.rcl_count[0], RES_THREADS, smem, st>>>(b, n_hb, n_or);
+        } else {
+            e = ensure_smem((const void*)k_resident<float>, smem);
+            if (e != cudaSuccess) return e;
+            k_resident<float><<<b.rcl_count[0], RES_THREADS, smem, st>>>(b, n_hb, n_or);
+        }
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    for (int g = 1; g < 4; ++g) {
+        if (b.rcl_count[g] == 0) continue;
+        e = fp64 ? launch_cl<double>(b, g, n_hb, n_or, st) : launch_cl<float>(b, g, n_hb, n_or, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace ptk

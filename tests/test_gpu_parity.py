@@ -250,7 +250,7 @@ def test_uneven_batch_parity():
     eng.close()
 
 
-@pytest.mark.parametrize("L", [8, 16])
+@pytest.mark.parametrize("L", [8, 16, 24, 32])
 def test_resident_and_streaming_paths_fp64(L):
     """A block of 1 heat-bath + 3 overrelaxation sweeps through the
     shared-memory resident kernel and through the streaming half sweeps gives
@@ -285,8 +285,11 @@ def test_resident_and_streaming_paths_fp64(L):
     assert np.abs(res["resident"] - res["streaming"]).max() <= 1e-14
 
 
-def test_resident_and_streaming_paths_fp32():
-    L, S, C, NT, seed = 16, 2, 2, 3, 63
+@pytest.mark.parametrize("L", [16, 24, 32])
+def test_resident_and_streaming_paths_fp32(L):
+    """L = 16 runs in one CTA per replica, L = 24 and 32 in clusters of 2 and
+    4 CTAs (slabs of z planes)."""
+    S, C, NT, seed = 2, 2, 3, 63
     res = {}
     for policy in ("resident", "streaming"):
         eng, J, B = make_engine(L, S, NT, C, "fp32", seed=seed)
