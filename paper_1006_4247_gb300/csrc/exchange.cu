@@ -113,6 +113,33 @@ __device__ __forceinline__ void slice(int n, int rank, int cs, int& lo, int& hi)
     hi = (int)(((long long)n * (rank + 1)) / cs);
 }
 
+// Row indices of the V-site vector at h0 of colour `color` (the layout of the
+// half sweeps): wrapped x neighbour, y and z neighbour rows, checkerboard
+// offset p and the row number.
+struct VRow {
+    int xs, hyp, hym, hzp, hzm, p, row, ih0;
+};
+
+template <int V>
+__device__ __forceinline__ VRow vrow(const SampleDesc& sd, int color, int h0) {
+    const int hL = sd.hL, L = sd.L;
+    VRow q;
+    q.row = (int)fdiv((uint32_t)h0, sd.div_hL);
+    q.ih0 = h0 - q.row * hL;
+    const int k = (int)fdiv((uint32_t)q.row, sd.div_L);
+    const int j = q.row - k * L;
+    q.p = (j + k + color) & 1;
+    const int rb = q.row * hL;
+    q.xs = q.p ? rb + ((q.ih0 + V == hL) ? 0 : q.ih0 + V) : rb + ((q.ih0 == 0) ? hL - 1 : q.ih0 - 1);
+    const int jp = (j + 1 == L) ? 0 : j + 1, jm = (j == 0) ? L - 1 : j - 1;
+    const int kp = (k + 1 == L) ? 0 : k + 1, km = (k == 0) ? L - 1 : k - 1;
+    q.hyp = q.ih0 + hL * (jp + L * k);
+    q.hym = q.ih0 + hL * (jm + L * k);
+    q.hzp = q.ih0 + hL * (j + L * kp);
+    q.hzm = q.ih0 + hL * (j + L * km);
+    return q;
+}
+
 // ---------------------------------------------------------------------------
 // Standard swap: Delta = (b_{i+1} - b_i)(H_{i+1} - H_i) in double.  No
 // lattice work: one warp per chain.
@@ -162,8 +189,12 @@ __device__ __forceinline__ T decim_D(T n, T b1, T b2, T db, T lr) {
 // swap temperatures and the decimated colour of both is redrawn by heat bath
 // at its new beta (purpose 2), which also yields the new energies.
 // ---------------------------------------------------------------------------
+template <typename T, int V>
+__device__ __forceinline__ void decimation_chain(const DevBatch& a, cg::cluster_group& cl, ChainSmem& sm,
+                                                 const ChainDesc& cd, const SampleDesc& sd, int ch, int cs, int rank);
+
 template <typename T>
-__global__ void __launch_bounds__(EX_THREADS) k_exchange_decimation(DevBatch a) {
+__global__ void __launch_bounds__(EX_THREADS, 2) k_exchange_decimation(DevBatch a) {
     __shared__ ChainSmem sm;
     cg::cluster_group cl = cg::this_cluster();
     const int cs = (int)cl.num_blocks(), rank = (int)cl.block_rank();
@@ -172,8 +203,24 @@ __global__ void __launch_bounds__(EX_THREADS) k_exchange_decimation(DevBatch a) 
     const SampleDesc& sd = a.samples[cd.s];
     const int NT = sd.NT, half = sd.half;
     load_chain(a, cd, NT, sm, ch);
+    if (sd.vec == 4) decimation_chain<T, (sizeof(T) == 4 ? 4 : 2)>(a, cl, sm, cd, sd, ch, cs, rank);
+    else if (sd.vec == 2) decimation_chain<T, 2>(a, cl, sm, cd, sd, ch, cs, rank);
+    else decimation_chain<T, 1>(a, cl, sm, cd, sd, ch, cs, rank);
+    if (rank == 0) store_chain(a, cd, NT, sm, ch);
+    cl.sync();  // no CTA leaves while others may still read its shared memory
+}
+
+// The pair walk of one chain; this CTA handles its slice of the V-site
+// vectors of the decimated colour (16-byte loads of the neighbour rows).
+template <typename T, int V>
+__device__ __forceinline__ void decimation_chain(const DevBatch& a, cg::cluster_group& cl, ChainSmem& sm,
+                                                 const ChainDesc& cd, const SampleDesc& sd, int ch, int cs,
+                                                 int rank) {
+    const int NT = sd.NT, half = sd.half;
     int lo, hi;
-    slice(half, rank, cs, lo, hi);
+    slice(half / V, rank, cs, lo, hi);  // in vectors
+    lo *= V;
+    hi *= V;
     int pub = 0;
     const unsigned long long step = *a.d_step;
     const double* beta = a.betas + sd.beta_off;
@@ -191,12 +238,17 @@ __global__ void __launch_bounds__(EX_THREADS) k_exchange_decimation(DevBatch a) 
         const T dbt = (T)(b2 - b1);
         const T lr = b1 > 0.0 ? (T)log(b2 / b1) : (T)0;
         T part[1] = {(T)0};
-        for (int h = lo + (int)threadIdx.x; h < hi; h += blockDim.x) {
-            const Site st = site_of(sd, d, h);
-            const V3<T> S1 = local_field<T>(st, half, c1 + (1 - d) * 3 * half, Jd, Jk);
-            const V3<T> S2 = local_field<T>(st, half, c2 + (1 - d) * 3 * half, Jd, Jk);
-            const T na = M<T>::sqrt_(dot(S1, S1)), nb = M<T>::sqrt_(dot(S2, S2));
-            part[0] += decim_D<T>(na, b1t, b2t, dbt, lr) - decim_D<T>(nb, b1t, b2t, dbt, lr);
+        for (int h0 = lo + (int)threadIdx.x * V; h0 < hi; h0 += (int)blockDim.x * V) {
+            const VRow q = vrow<V>(sd, d, h0);
+            T S1[3][V], S2[3][V];
+            nbr_field<T, V>(c1 + (1 - d) * 3 * half, Jd, Jk, half, h0, q.xs, q.hyp, q.hym, q.hzp, q.hzm, q.p, S1);
+            nbr_field<T, V>(c2 + (1 - d) * 3 * half, Jd, Jk, half, h0, q.xs, q.hyp, q.hym, q.hzp, q.hzm, q.p, S2);
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const T na = M<T>::sqrt_(S1[0][v] * S1[0][v] + S1[1][v] * S1[1][v] + S1[2][v] * S1[2][v]);
+                const T nb = M<T>::sqrt_(S2[0][v] * S2[0][v] + S2[1][v] * S2[1][v] + S2[2][v] * S2[2][v]);
+                part[0] += decim_D<T>(na, b1t, b2t, dbt, lr) - decim_D<T>(nb, b1t, b2t, dbt, lr);
+            }
         }
         cluster_sum<T, 1>(cl, sm, part, pub);
         if (threadIdx.x == 0) {
@@ -219,18 +271,29 @@ __global__ void __launch_bounds__(EX_THREADS) k_exchange_decimation(DevBatch a) 
             T* n1 = pool + (long long)sm.buf[i] * (6LL * half);      // now at b1
             T* n2 = pool + (long long)sm.buf[i + 1] * (6LL * half);  // now at b2
             const uint32_t id1 = (uint32_t)(cd.copy * NT + i), id2 = id1 + 1u;
-            for (int h = lo + (int)threadIdx.x; h < hi; h += blockDim.x) {
-                const Site st = site_of(sd, d, h);
-                const V3<T> S1 = local_field<T>(st, half, n1 + (1 - d) * 3 * half, Jd, Jk);
-                const uint4 w1 = rng_words(a.seed, (uint32_t)cd.s, (uint32_t)st.x, id1, step, 2u);
-                const V3<T> s1 = hb_site<T>(b1t, S1, w1.x, w1.y);
-                st3(n1 + d * 3 * half, half, h, s1);
-                e[0] -= dot(s1, S1);
-                const V3<T> S2 = local_field<T>(st, half, n2 + (1 - d) * 3 * half, Jd, Jk);
-                const uint4 w2 = rng_words(a.seed, (uint32_t)cd.s, (uint32_t)st.x, id2, step, 2u);
-                const V3<T> s2 = hb_site<T>(b2t, S2, w2.x, w2.y);
-                st3(n2 + d * 3 * half, half, h, s2);
-                e[1] -= dot(s2, S2);
+            for (int h0 = lo + (int)threadIdx.x * V; h0 < hi; h0 += (int)blockDim.x * V) {
+                const VRow q = vrow<V>(sd, d, h0);
+#pragma unroll
+                for (int which = 0; which < 2; ++which) {
+                    T* nb_ = which ? n2 : n1;
+                    const T bt = which ? b2t : b1t;
+                    const uint32_t id = which ? id2 : id1;
+                    T S[3][V];
+                    nbr_field<T, V>(nb_ + (1 - d) * 3 * half, Jd, Jk, half, h0, q.xs, q.hyp, q.hym, q.hzp, q.hzm,
+                                    q.p, S);
+                    T out[3][V];
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        const V3<T> Sv = {S[0][v], S[1][v], S[2][v]};
+                        const uint32_t x = (uint32_t)(2 * (q.ih0 + v) + q.p + sd.L * q.row);
+                        const uint4 w = rng_words(a.seed, (uint32_t)cd.s, x, id, step, 2u);
+                        const V3<T> sv = hb_site<T>(bt, Sv, w.x, w.y);
+                        out[0][v] = sv.x; out[1][v] = sv.y; out[2][v] = sv.z;
+                        e[which] -= dot(sv, Sv);
+                    }
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) stv<T, V>(nb_ + d * 3 * half + c * half + h0, out[c]);
+                }
             }
             cluster_sum<T, 2>(cl, sm, e, pub);
             if (threadIdx.x == 0) {
@@ -240,8 +303,6 @@ __global__ void __launch_bounds__(EX_THREADS) k_exchange_decimation(DevBatch a) 
             __syncthreads();
         }
     }
-    if (rank == 0) store_chain(a, cd, NT, sm, ch);
-    cl.sync();  // no CTA leaves while others may still read its shared memory
 }
 
 // ---------------------------------------------------------------------------
