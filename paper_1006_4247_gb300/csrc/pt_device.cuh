@@ -387,7 +387,12 @@ __device__ __forceinline__ void ldj(const float* __restrict__ p, float (&o)[V]) 
     else ldv_nc<float, V>(p, o);
 }
 
-template <typename T, int V, bool J_SHARED = false>
+// XSHFL: the row's vectors lie in consecutive lanes of the warp (all lanes
+// active), so the element just outside the vector -- the other colour's
+// first element of the next vector (p = 1) or last of the previous one
+// (p = 0), wrapping around the row -- is taken from lane `xs` by a shuffle
+// instead of a load (p is the same for every vector of a row).
+template <typename T, int V, bool J_SHARED = false, bool XSHFL = false>
 __device__ __forceinline__ void nbr_field(const T* __restrict__ oth, const float* __restrict__ Jown,
                                           const float* __restrict__ Joth, int half, int h0, int xs,
                                           int hyp, int hym, int hzp, int hzm, int p, T (&S)[3][V]) {
@@ -397,7 +402,8 @@ __device__ __forceinline__ void nbr_field(const T* __restrict__ oth, const float
         {
             float jx[V];
             ldj<J_SHARED, V>(Joth + h0, jx);
-            const float jxs = J_SHARED ? Joth[xs] : __ldg(Joth + xs);
+            const float jxs = XSHFL ? __shfl_sync(0xFFFFFFFFu, jx[V - 1], xs)
+                                    : (J_SHARED ? Joth[xs] : __ldg(Joth + xs));
 #pragma unroll
             for (int v = 0; v < V; ++v) jm[v] = p ? jx[v] : (v == 0 ? jxs : jx[v - 1]);
         }
@@ -406,7 +412,7 @@ __device__ __forceinline__ void nbr_field(const T* __restrict__ oth, const float
             const T* o = oth + c * half;
             T O[V];
             ldv<T, V>(o + h0, O);
-            const T os = o[xs];
+            const T os = XSHFL ? __shfl_sync(0xFFFFFFFFu, p ? O[0] : O[V - 1], xs) : o[xs];
 #pragma unroll
             for (int v = 0; v < V; ++v) {
                 const T xp = p ? (v == V - 1 ? os : O[v + 1]) : O[v];

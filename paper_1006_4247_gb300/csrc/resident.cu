@@ -87,8 +87,18 @@ struct VecIdx {
     int h0, xs0, xs1, hyp, hym, hzp, hzm, p0;
 };
 
+// Source lanes of the wrapped x neighbour when a warp holds whole rows of
+// n = hL / V vectors: the next vector's lane (p = 1) or the previous one's
+// (p = 0), wrapping within the row.
 template <int V>
-__device__ __forceinline__ VecIdx vec_idx(const SampleDesc& sd, int h0) {
+__device__ __forceinline__ void xs_lanes(int hL, int ih0, int& right, int& left) {
+    const int lane = (int)(threadIdx.x & 31u), n = hL / V, m = ih0 / V;  // m: vector index in the row
+    right = (m == n - 1) ? lane - (n - 1) : lane + 1;
+    left = (m == 0) ? lane + (n - 1) : lane - 1;
+}
+
+template <int V>
+__device__ __forceinline__ VecIdx vec_idx(const SampleDesc& sd, int h0, bool xshfl) {
     const int hL = sd.hL, L = sd.L;
     VecIdx q;
     q.h0 = h0;
@@ -98,7 +108,8 @@ __device__ __forceinline__ VecIdx vec_idx(const SampleDesc& sd, int h0) {
     const int j = row - k * L;
     q.p0 = (j + k) & 1;
     const int rb = row * hL;
-    const int left = rb + ((ih0 == 0) ? hL - 1 : ih0 - 1), right = rb + ((ih0 + V == hL) ? 0 : ih0 + V);
+    int left = rb + ((ih0 == 0) ? hL - 1 : ih0 - 1), right = rb + ((ih0 + V == hL) ? 0 : ih0 + V);
+    if (xshfl) xs_lanes<V>(hL, ih0, right, left);  // lanes instead of indices
     q.xs0 = q.p0 ? right : left;   // colour 0: p = p0
     q.xs1 = q.p0 ? left : right;   // colour 1: p = 1 - p0
     const int jp = (j + 1 == L) ? 0 : j + 1, jm = (j == 0) ? L - 1 : j - 1;
@@ -112,7 +123,7 @@ __device__ __forceinline__ VecIdx vec_idx(const SampleDesc& sd, int h0) {
 
 // Overrelaxation half sweep when every thread owns at most one vector of a
 // colour (half <= threads * V): the indices come precomputed.
-template <typename T, int V, bool ENERGY>
+template <typename T, int V, bool ENERGY, bool XSHFL>
 __device__ __forceinline__ T res_or_one(T* __restrict__ sm, const float* __restrict__ J, int half, int color,
                                         const VecIdx& q) {
     T e = (T)0;
@@ -124,7 +135,7 @@ __device__ __forceinline__ T res_or_one(T* __restrict__ sm, const float* __restr
         const int p = q.p0 ^ color;
         const int xs = color ? q.xs1 : q.xs0;
         T S[3][V];
-        nbr_field<T, V, true>(oth, Jown, Joth, half, q.h0, xs, q.hyp, q.hym, q.hzp, q.hzm, p, S);
+        nbr_field<T, V, true, XSHFL>(oth, Jown, Joth, half, q.h0, xs, q.hyp, q.hym, q.hzp, q.hzm, p, S);
         T s[3][V];
 #pragma unroll
         for (int c = 0; c < 3; ++c) ldv<T, V>(own + c * half + q.h0, s[c]);
@@ -163,11 +174,18 @@ __device__ __forceinline__ T res_block(T* sm, const float* J, const DevBatch& a,
             __syncthreads();
         }
     if (sd.half <= RES_THREADS * V) {
-        const VecIdx q = vec_idx<V>(sd, (int)threadIdx.x * V);
+        // whole rows per warp and every lane active: wrapped x neighbours by shuffle
+        const bool xsh = (32 % (sd.hL / V) == 0) && ((sd.half / V) % 32 == 0);
+        const VecIdx q = vec_idx<V>(sd, (int)threadIdx.x * V, xsh);
         for (int o = 0; o < n_or; ++o)
             for (int c = 0; c < 2; ++c, ++kstep) {
-                if (kstep == total - 1) e = res_or_one<T, V, true>(sm, J, sd.half, c, q);
-                else res_or_one<T, V, false>(sm, J, sd.half, c, q);
+                if (xsh) {
+                    if (kstep == total - 1) e = res_or_one<T, V, true, true>(sm, J, sd.half, c, q);
+                    else res_or_one<T, V, false, true>(sm, J, sd.half, c, q);
+                } else {
+                    if (kstep == total - 1) e = res_or_one<T, V, true, false>(sm, J, sd.half, c, q);
+                    else res_or_one<T, V, false, false>(sm, J, sd.half, c, q);
+                }
                 __syncthreads();
             }
         return e;
@@ -242,17 +260,17 @@ constexpr int CL_THREADS = 1024;
 // Neighbour field of V sites of a slab row; the z+ row may live in the next
 // CTA (othP) and the z- row with its couplings in the previous one (othM,
 // JothM); all pointers address [component][hl] arrays of the other colour.
-template <typename T, int V>
+template <typename T, int V, bool XSHFL = false>
 __device__ __forceinline__ void nbr_field_cl(const T* oth, const float* Jown, const float* Joth, int hl, int h0,
                                              int xs, int hyp, int hym, const T* othP, int hzp, const T* othM,
                                              const float* JothM, int hzm, int p, T (&S)[3][V]) {
-    {   // +-x: the same row of the other colour, shifted by one (plus xs)
+    {   // +-x: the same row of the other colour, shifted by one (plus xs: an index, or with XSHFL a lane)
         float jp[V], jm[V];
         ldv<float, V>(Jown + h0, jp);
         {
             float jx[V];
             ldv<float, V>(Joth + h0, jx);
-            const float jxs = Joth[xs];
+            const float jxs = XSHFL ? __shfl_sync(0xFFFFFFFFu, jx[V - 1], xs) : Joth[xs];
 #pragma unroll
             for (int v = 0; v < V; ++v) jm[v] = p ? jx[v] : (v == 0 ? jxs : jx[v - 1]);
         }
@@ -261,7 +279,7 @@ __device__ __forceinline__ void nbr_field_cl(const T* oth, const float* Jown, co
             const T* o = oth + c * hl;
             T O[V];
             ldv<T, V>(o + h0, O);
-            const T os = o[xs];
+            const T os = XSHFL ? __shfl_sync(0xFFFFFFFFu, p ? O[0] : O[V - 1], xs) : o[xs];
 #pragma unroll
             for (int v = 0; v < V; ++v) {
                 const T xp = p ? (v == V - 1 ? os : O[v + 1]) : O[v];
@@ -359,7 +377,7 @@ struct VecIdxCl {
 };
 
 template <int V>
-__device__ __forceinline__ VecIdxCl vec_idx_cl(const SampleDesc& sd, const Slab& sb, int h0) {
+__device__ __forceinline__ VecIdxCl vec_idx_cl(const SampleDesc& sd, const Slab& sb, int h0, bool xshfl) {
     const int hL = sd.hL, L = sd.L;
     VecIdxCl q;
     q.h0 = h0;
@@ -369,7 +387,8 @@ __device__ __forceinline__ VecIdxCl vec_idx_cl(const SampleDesc& sd, const Slab&
     const int j = row - kl * L;
     const int p0 = (j + sb.k0 + kl) & 1;
     const int rb = row * hL;
-    const int left = rb + ((ih0 == 0) ? hL - 1 : ih0 - 1), right = rb + ((ih0 + V == hL) ? 0 : ih0 + V);
+    int left = rb + ((ih0 == 0) ? hL - 1 : ih0 - 1), right = rb + ((ih0 + V == hL) ? 0 : ih0 + V);
+    if (xshfl) xs_lanes<V>(hL, ih0, right, left);  // lanes instead of indices
     q.xs0 = p0 ? right : left;
     q.xs1 = p0 ? left : right;
     const int jp = (j + 1 == L) ? 0 : j + 1, jm = (j == 0) ? L - 1 : j - 1;
@@ -385,7 +404,7 @@ __device__ __forceinline__ VecIdxCl vec_idx_cl(const SampleDesc& sd, const Slab&
 // Overrelaxation half sweep of the slab with precomputed indices; the
 // neighbour CTAs' arrays are mapped only by the warps of the boundary planes
 // (a warp's vectors lie in one plane, so the branch is uniform).
-template <typename T, int V, bool ENERGY>
+template <typename T, int V, bool ENERGY, bool XSHFL>
 __device__ __forceinline__ T cl_or_one(cg::cluster_group& cl, T* __restrict__ sm, const float* __restrict__ J,
                                        int hl, int rank, int cs, int color, const VecIdxCl& q) {
     T e = (T)0;
@@ -406,7 +425,8 @@ __device__ __forceinline__ T cl_or_one(cg::cluster_group& cl, T* __restrict__ sm
             JothM = cl.map_shared_rank(const_cast<float*>(Joth), rm);
         }
         T S[3][V];
-        nbr_field_cl<T, V>(oth, Jown, Joth, hl, q.h0, xs, q.hyp, q.hym, othP, q.hzp, othM, JothM, q.hzm, p, S);
+        nbr_field_cl<T, V, XSHFL>(oth, Jown, Joth, hl, q.h0, xs, q.hyp, q.hym, othP, q.hzp, othM, JothM, q.hzm, p,
+                                  S);
         T s[3][V];
 #pragma unroll
         for (int c = 0; c < 3; ++c) ldv<T, V>(own + c * hl + q.h0, s[c]);
@@ -444,11 +464,17 @@ __device__ __forceinline__ T cl_block(cg::cluster_group& cl, T* sm, const float*
             cl.sync();
         }
     if (sb.hl <= CL_THREADS * V) {
-        const VecIdxCl q = vec_idx_cl<V>(sd, sb, (int)threadIdx.x * V);
+        const bool xsh = (32 % (sd.hL / V) == 0) && ((sb.hl / V) % 32 == 0);
+        const VecIdxCl q = vec_idx_cl<V>(sd, sb, (int)threadIdx.x * V, xsh);
         for (int o = 0; o < n_or; ++o)
             for (int c = 0; c < 2; ++c, ++kstep) {
-                if (kstep == total - 1) e = cl_or_one<T, V, true>(cl, sm, J, sb.hl, sb.rank, sb.cs, c, q);
-                else cl_or_one<T, V, false>(cl, sm, J, sb.hl, sb.rank, sb.cs, c, q);
+                if (xsh) {
+                    if (kstep == total - 1) e = cl_or_one<T, V, true, true>(cl, sm, J, sb.hl, sb.rank, sb.cs, c, q);
+                    else cl_or_one<T, V, false, true>(cl, sm, J, sb.hl, sb.rank, sb.cs, c, q);
+                } else {
+                    if (kstep == total - 1) e = cl_or_one<T, V, true, false>(cl, sm, J, sb.hl, sb.rank, sb.cs, c, q);
+                    else cl_or_one<T, V, false, false>(cl, sm, J, sb.hl, sb.rank, sb.cs, c, q);
+                }
                 cl.sync();
             }
         return e;
