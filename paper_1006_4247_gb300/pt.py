@@ -387,8 +387,11 @@ class Engine:
     def set_policy(self, policy):
         pt_set_policy(self.h, policy)
 
-    def measure_device(self):
-        pt_measure_device(self.h)
+    def measure_device(self, d_energy=None, d_overlap=None, d_chi=None):
+        """Enqueue the reductions; results also go to the given device
+        tensors (float64, contiguous, the layouts of pt_measure), if any."""
+        ptr = lambda t: None if t is None else int(t.data_ptr())
+        pt_measure_device(self.h, ptr(d_energy), ptr(d_overlap), ptr(d_chi))
 
     def profile(self, enable=True):
         pt_profile(self.h, enable)

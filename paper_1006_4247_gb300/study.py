@@ -1,0 +1,149 @@
+"""The paper's measurement protocol (Sec. 4) on synthetic coupling sets.
+
+For one lattice size: ``n_sets`` Gaussian coupling sets, the geometric ladder
+of the paper (T from 0.12 to 0.19, N_T replicas), two copies per set, update
+cycles of 1 heat-bath + 5L/4 overrelaxation sweeps and one tempering update,
+run with each exchange method on the same sets.  Reported per method:
+
+* the acceptance of every pair (Table I gives the first and last pair);
+* the round-trip time t_R: sweeps of the run divided by the round trips of
+  all 2 N_T configurations of a set (Sec. 4.2);
+* the integrated autocorrelation time of the overlap susceptibility at the
+  lowest temperature, tau_int(chi) in sweeps, by automatic windowing (the
+  smallest window W with W >= c tau(W), c = 4; Sokal).
+
+The paper's coupling sets are not available, so the absolute values are not
+comparable with its tables; the ratios between methods are the result.  All
+work runs in the engine (C ABI); this module only drives it and reduces the
+measurements on the host.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+
+import numpy as np
+
+from . import ladder
+from . import pt
+from . import workloads
+
+T_MIN, T_MAX = 0.12, 0.19
+
+
+def paper_ladder(n_temps: int) -> np.ndarray:
+    """beta_i of the paper's geometric temperature ladder, ascending."""
+    return ladder.geometric(1.0 / T_MAX, 1.0 / T_MIN, n_temps)
+
+
+def tau_int(x: np.ndarray, c: float = 4.0) -> float:
+    """Integrated autocorrelation time (in samples) of a series by automatic
+    windowing: tau(W) = 1/2 + sum_{t=1}^{W} rho(t), the first W >= c tau(W)."""
+    x = np.asarray(x, np.float64)
+    n = x.size
+    if n < 8:
+        return float("nan")
+    y = x - x.mean()
+    f = np.fft.rfft(y, 2 * n)
+    acf = np.fft.irfft(f * np.conj(f))[:n]
+    if acf[0] <= 0:
+        return float("nan")
+    rho = acf / acf[0]
+    tau = 0.5
+    for W in range(1, n):
+        tau += rho[W]
+        if W >= c * tau:
+            return float(tau)
+    return float(tau)
+
+
+def run_method(L, couplings, betas, mode, eps, cycles, burn, seed=0):
+    """One engine run of all sets with one exchange method.  Returns the
+    acceptance per set and pair [S, NT-1], round trips per set [S] and the
+    chi series at the lowest temperature [cycles, S] (after the burn-in)."""
+    import torch
+    S = len(couplings)
+    NT = len(betas)
+    n_or = max(1, (5 * L) // 4)
+    stream = torch.cuda.Stream()
+    eng = pt.Engine(L, np.stack(couplings), np.broadcast_to(betas, (S, NT)).copy(), n_copies=2, seed=seed,
+                    stream=stream.cuda_stream)
+    try:
+        if eps is not None:
+            eng.set_params(None, np.broadcast_to(eps, (S, NT - 1)).astype(np.float32).copy())
+        eng.autotune(1, n_or)
+        eng.cycles(burn, 1, n_or, mode)
+        p0, a0, r0, _ = eng.stats()
+        chi = torch.empty((cycles, S * NT), dtype=torch.float64, device="cuda")
+        for k in range(cycles):
+            eng.cycles(1, 1, n_or, mode)
+            eng.measure_device(d_chi=chi[k])
+        torch.cuda.synchronize()
+        p1, a1, r1, _ = eng.stats()
+    finally:
+        eng.close()
+    acc = (a1 - a0).sum(1) / np.maximum((p1 - p0).sum(1), 1)  # pooled over the copies
+    rt = (r1 - r0).sum(1)
+    chi_min_T = chi.view(cycles, S, NT)[:, :, NT - 1].cpu().numpy()
+    return acc, rt, chi_min_T
+
+
+def protocol(L, n_temps, n_sets=10, cycles=20000, burn=5000, kappa=0.1, seed0=8000,
+             methods=("plain", "decimation", "coolheat")):
+    """The protocol for one L; returns a JSON-ready summary."""
+    J = [workloads.couplings(L, seed0 + 97 * L + k) for k in range(n_sets)]
+    b = paper_ladder(n_temps)
+    spc = 1 + max(1, (5 * L) // 4)  # sweeps per cycle
+    out = {"L": L, "n_temps": n_temps, "n_sets": n_sets, "cycles": cycles, "burn": burn,
+           "sweeps_per_cycle": spc, "kappa": kappa, "methods": {}}
+    for m in methods:
+        eps = None
+        if m == "coolheat":
+            bound = min(ladder.eps_bound(L, j) for j in J)
+            eps = ladder.eps_from_kappa(b, np.full(n_temps - 1, kappa), bound)
+        acc, rt, chi = run_method(L, J, b, m, eps, cycles, burn, seed=11)
+        tR = cycles * spc / np.maximum(rt, 1)
+        tau = np.array([tau_int(chi[:, s]) * spc for s in range(n_sets)])
+        out["methods"][m] = {
+            "acc_first_pair": [float(acc[:, 0].min()), float(acc[:, 0].max())],
+            "acc_last_pair": [float(acc[:, -1].min()), float(acc[:, -1].max())],
+            "acc_mean": float(acc.mean()),
+            "acc_profile": acc.mean(0).round(4).tolist(),
+            "t_R": [float(tR.min()), float(tR.max())],
+            "t_R_per_set": tR.round(1).tolist(),
+            "round_trips_per_set": rt.tolist(),
+            "tau_int_chi": [float(np.nanmin(tau)), float(np.nanmax(tau))],
+            "tau_int_chi_per_set": np.round(tau, 1).tolist(),
+        }
+    ms = out["methods"]
+    if "plain" in ms:
+        # speed-ups over the standard method, averaged over the sets (Table II)
+        tp = np.array(ms["plain"]["t_R_per_set"])
+        taup = np.array(ms["plain"]["tau_int_chi_per_set"])
+        for m in ms:
+            if m != "plain":
+                ms[m]["t_R_speedup_mean"] = float(np.mean(tp / np.array(ms[m]["t_R_per_set"])))
+                r = taup / np.array(ms[m]["tau_int_chi_per_set"])
+                ms[m]["tau_speedup_mean"] = float(np.nanmean(r))
+                ms[m]["tau_speedup_median"] = float(np.nanmedian(r))  # robust to sets not yet equilibrated
+                ms[m]["acc_ratio"] = ms[m]["acc_mean"] / ms["plain"]["acc_mean"]
+    return out
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description="the paper's protocol on synthetic coupling sets")
+    ap.add_argument("--L", type=int, default=16)
+    ap.add_argument("--n-temps", type=int, default=0, help="0: the paper's N_T (15, 27, 43 at L = 16, 24, 32)")
+    ap.add_argument("--sets", type=int, default=10)
+    ap.add_argument("--cycles", type=int, default=20000)
+    ap.add_argument("--burn", type=int, default=5000)
+    ap.add_argument("--kappa", type=float, default=0.1)
+    ap.add_argument("--methods", default="plain,decimation,coolheat")
+    a = ap.parse_args(argv)
+    nt = a.n_temps or {16: 15, 24: 27, 32: 43}.get(a.L, ladder.default_n_temps(a.L, 1 / T_MAX, 1 / T_MIN))
+    print(json.dumps(protocol(a.L, nt, a.sets, a.cycles, a.burn, a.kappa, methods=tuple(a.methods.split(",")))))
+
+
+if __name__ == "__main__":
+    main()
