@@ -113,33 +113,6 @@ __device__ __forceinline__ void slice(int n, int rank, int cs, int& lo, int& hi)
     hi = (int)(((long long)n * (rank + 1)) / cs);
 }
 
-// Row indices of the V-site vector at h0 of colour `color` (the layout of the
-// half sweeps): wrapped x neighbour, y and z neighbour rows, checkerboard
-// offset p and the row number.
-struct VRow {
-    int xs, hyp, hym, hzp, hzm, p, row, ih0;
-};
-
-template <int V>
-__device__ __forceinline__ VRow vrow(const SampleDesc& sd, int color, int h0) {
-    const int hL = sd.hL, L = sd.L;
-    VRow q;
-    q.row = (int)fdiv((uint32_t)h0, sd.div_hL);
-    q.ih0 = h0 - q.row * hL;
-    const int k = (int)fdiv((uint32_t)q.row, sd.div_L);
-    const int j = q.row - k * L;
-    q.p = (j + k + color) & 1;
-    const int rb = q.row * hL;
-    q.xs = q.p ? rb + ((q.ih0 + V == hL) ? 0 : q.ih0 + V) : rb + ((q.ih0 == 0) ? hL - 1 : q.ih0 - 1);
-    const int jp = (j + 1 == L) ? 0 : j + 1, jm = (j == 0) ? L - 1 : j - 1;
-    const int kp = (k + 1 == L) ? 0 : k + 1, km = (k == 0) ? L - 1 : k - 1;
-    q.hyp = q.ih0 + hL * (jp + L * k);
-    q.hym = q.ih0 + hL * (jm + L * k);
-    q.hzp = q.ih0 + hL * (j + L * kp);
-    q.hzm = q.ih0 + hL * (j + L * km);
-    return q;
-}
-
 // ---------------------------------------------------------------------------
 // Standard swap: Delta = (b_{i+1} - b_i)(H_{i+1} - H_i) in double.  No
 // lattice work: one warp per chain.

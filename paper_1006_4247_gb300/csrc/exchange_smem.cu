@@ -82,6 +82,62 @@ __device__ __forceinline__ T sx_decim_D(T n, T b1, T b2, T db, T lr) {
     return ln_sinhc<T>(R2) - ln_sinhc<T>(R1);
 }
 
+// One pass of the cooling sweep of s1 and the heating sweep of s2 over V-site
+// vectors (16- or 8-byte shared-memory loads of the neighbour rows).  Pass 0
+// cools colour 0 of s1 (field from colour 1 of s1) into f1 and heats colour 1
+// of s2 (field from colour 0 of s2) into f2; pass 1 cools colour 1 (field
+// from the cooled colour 0 in f1) and heats colour 0 (field from the heated
+// colour 1 in f2), and sums the energies of the two transforms.
+template <typename T, int V>
+__device__ __forceinline__ void ch_pass(const SampleDesc& sd, const T* s1, const T* s2, T* f1, T* f2,
+                                        const float* J0, const float* J1, T eps, int pass, T& lj1, T& lj2, T& hc,
+                                        T& hh) {
+    const int half = sd.half;
+    const int cc = pass, hcol = 1 - pass;  // colour cooled, colour heated
+    const T* cfield = pass == 0 ? s1 + 3 * half : f1;
+    const T* hfield = pass == 0 ? s2 : f2 + 3 * half;
+    const float* Jc_own = cc ? J1 : J0;
+    const float* Jc_oth = cc ? J0 : J1;
+    const float* Jh_own = hcol ? J1 : J0;
+    const float* Jh_oth = hcol ? J0 : J1;
+    for (int h0 = (int)threadIdx.x * V; h0 < half; h0 += (int)blockDim.x * V) {
+        {
+            const VRow q = vrow<V>(sd, cc, h0);
+            T S[3][V], s[3][V];
+            nbr_field<T, V>(cfield, Jc_own, Jc_oth, half, h0, q.xs, q.hyp, q.hym, q.hzp, q.hzm, q.p, S);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) ldv<T, V>(s1 + cc * 3 * half + c * half + h0, s[c]);
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const V3<T> Sv = {S[0][v], S[1][v], S[2][v]};
+                V3<T> sv = {s[0][v], s[1][v], s[2][v]};
+                lj1 += cool_site<T>(eps, Sv, sv);
+                if (pass == 1) hc -= dot(sv, Sv);
+                s[0][v] = sv.x; s[1][v] = sv.y; s[2][v] = sv.z;
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) stv<T, V>(f1 + cc * 3 * half + c * half + h0, s[c]);
+        }
+        {
+            const VRow q = vrow<V>(sd, hcol, h0);
+            T S[3][V], u[3][V];
+            nbr_field<T, V>(hfield, Jh_own, Jh_oth, half, h0, q.xs, q.hyp, q.hym, q.hzp, q.hzm, q.p, S);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) ldv<T, V>(s2 + hcol * 3 * half + c * half + h0, u[c]);
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const V3<T> Sv = {S[0][v], S[1][v], S[2][v]};
+                V3<T> uv = {u[0][v], u[1][v], u[2][v]};
+                lj2 += heat_site<T>(eps, Sv, uv);
+                if (pass == 1) hh -= dot(uv, Sv);
+                u[0][v] = uv.x; u[1][v] = uv.y; u[2][v] = uv.z;
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) stv<T, V>(f2 + hcol * 3 * half + c * half + h0, u[c]);
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Cooling/heating: slots hold s1 (now at beta_i), s2 (at beta_{i+1}) and the
 // transforms f1 = C(s1), f2 = C^-1(s2).  Accept: f2 is final at beta_i and is
@@ -120,33 +176,12 @@ __global__ void __launch_bounds__(SX_THREADS, 1) k_exchange_coolheat_smem(DevBat
         T* f1 = slot(F1);
         T* f2 = slot(F2);
         T lj1 = (T)0, lj2 = (T)0, hc = (T)0, hh = (T)0;  // per-thread partials of a few sites
-        for (int h = threadIdx.x; h < half; h += blockDim.x) {
-            const Site st0 = site_of(sd, 0, h);
-            const V3<T> S = local_field<T>(st0, half, s1 + 3 * half, J0, J1);
-            V3<T> s = ld3(s1, half, h);
-            lj1 += cool_site<T>(eps, S, s);
-            st3(f1, half, h, s);
-            const Site st1 = site_of(sd, 1, h);
-            const V3<T> S2 = local_field<T>(st1, half, s2, J1, J0);
-            V3<T> u = ld3(s2 + 3 * half, half, h);
-            lj2 += heat_site<T>(eps, S2, u);
-            st3(f2 + 3 * half, half, h, u);
-        }
+        const bool v2 = (sd.hL % 2) == 0;  // 2-site vectors where the row length allows
+        if (v2) ch_pass<T, 2>(sd, s1, s2, f1, f2, J0, J1, eps, 0, lj1, lj2, hc, hh);
+        else ch_pass<T, 1>(sd, s1, s2, f1, f2, J0, J1, eps, 0, lj1, lj2, hc, hh);
         __syncthreads();
-        for (int h = threadIdx.x; h < half; h += blockDim.x) {
-            const Site st1 = site_of(sd, 1, h);
-            const V3<T> S = local_field<T>(st1, half, f1, J1, J0);
-            V3<T> s = ld3(s1 + 3 * half, half, h);
-            lj1 += cool_site<T>(eps, S, s);
-            st3(f1 + 3 * half, half, h, s);
-            hc -= dot(s, S);
-            const Site st0 = site_of(sd, 0, h);
-            const V3<T> S2 = local_field<T>(st0, half, f2 + 3 * half, J0, J1);
-            V3<T> u = ld3(s2, half, h);
-            lj2 += heat_site<T>(eps, S2, u);
-            st3(f2, half, h, u);
-            hh -= dot(u, S2);
-        }
+        if (v2) ch_pass<T, 2>(sd, s1, s2, f1, f2, J0, J1, eps, 1, lj1, lj2, hc, hh);
+        else ch_pass<T, 1>(sd, s1, s2, f1, f2, J0, J1, eps, 1, lj1, lj2, hc, hh);
         const T part[4] = {lj1, lj2, hc, hh};
         double tot[4];
         block_sum_multi<T, 4>(part, tot, sm.red);
