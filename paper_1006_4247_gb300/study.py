@@ -59,15 +59,17 @@ def tau_int(x: np.ndarray, c: float = 4.0) -> float:
 
 
 def run_method(L, couplings, betas, mode, eps, cycles, burn, seed=0):
-    """One engine run of all sets with one exchange method.  Returns the
-    acceptance per set and pair [S, NT-1], round trips per set [S] and the
-    chi series at the lowest temperature [cycles, S] (after the burn-in)."""
+    """One engine run of all sets with one exchange method; betas [NT] or per
+    set [S, NT], eps [NT-1] or [S, NT-1] (or None).  Returns the acceptance
+    per set and pair [S, NT-1], round trips per set [S] and the chi series at
+    the lowest temperature [cycles, S] (after the burn-in)."""
     import torch
     S = len(couplings)
-    NT = len(betas)
+    B = np.asarray(betas, np.float64)
+    NT = B.shape[-1]
     n_or = max(1, (5 * L) // 4)
     stream = torch.cuda.Stream()
-    eng = pt.Engine(L, np.stack(couplings), np.broadcast_to(betas, (S, NT)).copy(), n_copies=2, seed=seed,
+    eng = pt.Engine(L, np.stack(couplings), np.broadcast_to(B, (S, NT)).copy(), n_copies=2, seed=seed,
                     stream=stream.cuda_stream)
     try:
         if eps is not None:
@@ -131,6 +133,49 @@ def protocol(L, n_temps, n_sets=10, cycles=20000, burn=5000, kappa=0.1, seed0=80
     return out
 
 
+def replicas(L, n_temps_list, reference_nt, n_sets=10, cycles=20000, burn=5000, kappa=0.1, seed0=8000):
+    """Round-trip time against the number of replicas (the
+    paper's reduced-N_T test generalised) for: the standard swap, decimation
+    and cooling/heating on the geometric ladder (one kappa), and
+    cooling/heating on the ladders and epsilons the learned network proposes
+    for each set.  Returns t_R per (arm, N_T) (mean over sets, sweeps) and,
+    per arm, the smallest N_T whose t_R is not above the standard method's at
+    reference_nt."""
+    J = [workloads.couplings(L, seed0 + 97 * L + k) for k in range(n_sets)]
+    spc = 1 + max(1, (5 * L) // 4)
+    net = ladder.LearnedLadder.load()
+    arms = ("plain", "decimation", "coolheat", "coolheat_learned")
+    out = {"L": L, "reference_nt": reference_nt, "n_sets": n_sets, "cycles": cycles, "burn": burn,
+           "sweeps_per_cycle": spc, "t_R": {a: {} for a in arms}, "acc_min": {a: {} for a in arms},
+           "t_R_se": {a: {} for a in arms}}
+    try:
+        for nt in sorted(set(list(n_temps_list) + [reference_nt])):
+            b = paper_ladder(nt)
+            for arm in arms:
+                if arm == "plain" and nt != reference_nt and nt < min(n_temps_list):
+                    continue
+                mode = "coolheat" if arm.startswith("coolheat") else arm
+                eps = None
+                betas = b
+                if arm == "coolheat":
+                    bound = min(ladder.eps_bound(L, j) for j in J)
+                    eps = ladder.eps_from_kappa(b, np.full(nt - 1, kappa), bound)
+                elif arm == "coolheat_learned":
+                    prop = net.propose_many([(L, j, 1 / T_MAX, 1 / T_MIN) for j in J], n_temps=nt)
+                    betas = np.stack([p[0] for p in prop])
+                    eps = np.stack([p[1] for p in prop])
+                acc, rt, _ = run_method(L, J, betas, mode, eps, cycles, burn, seed=13)
+                tR = cycles * spc / np.maximum(rt, 1)
+                out["t_R"][arm][nt] = float(tR.mean())
+                out["t_R_se"][arm][nt] = float(tR.std(ddof=1) / math.sqrt(n_sets))
+                out["acc_min"][arm][nt] = float(acc.min(1).mean())
+    finally:
+        net.close()
+    ref = out["t_R"]["plain"][reference_nt]
+    out["replicas_needed"] = {a: min([nt for nt, t in out["t_R"][a].items() if t <= ref], default=None) for a in arms}
+    return out
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description="the paper's protocol on synthetic coupling sets")
     ap.add_argument("--L", type=int, default=16)
@@ -140,9 +185,14 @@ def main(argv=None):
     ap.add_argument("--burn", type=int, default=5000)
     ap.add_argument("--kappa", type=float, default=0.1)
     ap.add_argument("--methods", default="plain,decimation,coolheat")
+    ap.add_argument("--replicas", default="", help="comma-separated N_T list: run the replica-count study")
     a = ap.parse_args(argv)
     nt = a.n_temps or {16: 15, 24: 27, 32: 43}.get(a.L, ladder.default_n_temps(a.L, 1 / T_MAX, 1 / T_MIN))
-    print(json.dumps(protocol(a.L, nt, a.sets, a.cycles, a.burn, a.kappa, methods=tuple(a.methods.split(",")))))
+    if a.replicas:
+        nts = [int(v) for v in a.replicas.split(",")]
+        print(json.dumps(replicas(a.L, nts, nt, a.sets, a.cycles, a.burn, a.kappa)))
+    else:
+        print(json.dumps(protocol(a.L, nt, a.sets, a.cycles, a.burn, a.kappa, methods=tuple(a.methods.split(",")))))
 
 
 if __name__ == "__main__":
