@@ -176,6 +176,59 @@ def replicas(L, n_temps_list, reference_nt, n_sets=10, cycles=20000, burn=5000, 
     return out
 
 
+def equilibration(L=16, n_temps=15, n_runs=2000, cycles=1000, kappa=0.1, seed=8500,
+                  methods=("plain", "decimation", "coolheat")):
+    """Equilibration from the ordered start (Sec. 4.4, Fig. 1):
+    n_runs independent runs (independent random numbers) on one coupling set,
+    every spin (1, 0, 0) at the start, all runs in one batched engine; the
+    mean and standard error over runs of chi at the lowest temperature after
+    every cycle.  Returns the curve at a few cycle counts per method and the
+    first cycle where the mean comes within 5% of its value over the last
+    tenth of the run."""
+    import torch
+    J = workloads.couplings(L, seed)
+    b = paper_ladder(n_temps)
+    n_or = max(1, (5 * L) // 4)
+    marks = [m for m in (1, 3, 10, 30, 100, 300, 1000, 3000) if m <= cycles]
+    out = {"L": L, "n_temps": n_temps, "runs": n_runs, "cycles": cycles, "marks": marks, "methods": {}}
+    for m in methods:
+        eps = None
+        if m == "coolheat":
+            eps = ladder.eps_from_kappa(b, np.full(n_temps - 1, kappa), ladder.eps_bound(L, J))
+        stream = torch.cuda.Stream()
+        eng = pt.Engine(L, np.broadcast_to(J, (n_runs,) + J.shape).copy(), np.broadcast_to(b, (n_runs, n_temps)).copy(),
+                        n_copies=2, seed=seed + 1, start="ordered", stream=stream.cuda_stream)
+        try:
+            if eps is not None:
+                eng.set_params(None, np.broadcast_to(eps, (n_runs, n_temps - 1)).astype(np.float32).copy())
+            chi = torch.empty((cycles, n_runs * n_temps), dtype=torch.float64, device="cuda")
+            for k in range(cycles):
+                eng.cycles(1, 1, n_or, m)
+                eng.measure_device(d_chi=chi[k])
+            torch.cuda.synchronize()
+        finally:
+            eng.close()
+        c = chi.view(cycles, n_runs, n_temps)[:, :, n_temps - 1]
+        mean = c.mean(1).cpu().numpy()
+        se = (c.std(1) / math.sqrt(n_runs)).cpu().numpy()
+        plateau = float(mean[-max(1, cycles // 10):].mean())
+        close = np.nonzero(np.abs(mean - plateau) <= 0.05 * abs(plateau))[0]
+        out["methods"][m] = {"chi": [float(mean[t - 1]) for t in marks], "se": [float(se[t - 1]) for t in marks],
+                             "plateau": plateau, "cycles_to_5pct": int(close[0]) + 1 if close.size else None,
+                             "curve_every_10": mean[9::10].round(3).tolist()}
+    if "plain" in out["methods"]:
+        # cycles each method needs to reach the standard method's chi after 30%, 100% of the run
+        ref = out["methods"]["plain"]["curve_every_10"]
+        for m, v in out["methods"].items():
+            cur = np.array(v["curve_every_10"])
+            v["cycles_to_reach_standard"] = {}
+            for frac in (0.3, 1.0):
+                target = ref[max(0, int(frac * len(ref)) - 1)]
+                hit = np.nonzero(cur >= target)[0]
+                v["cycles_to_reach_standard"][str(frac)] = int(10 * (hit[0] + 1)) if hit.size else None
+    return out
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description="the paper's protocol on synthetic coupling sets")
     ap.add_argument("--L", type=int, default=16)
@@ -186,9 +239,12 @@ def main(argv=None):
     ap.add_argument("--kappa", type=float, default=0.1)
     ap.add_argument("--methods", default="plain,decimation,coolheat")
     ap.add_argument("--replicas", default="", help="comma-separated N_T list: run the replica-count study")
+    ap.add_argument("--equilibration", type=int, default=0, help="runs of the equilibration study (0: off)")
     a = ap.parse_args(argv)
     nt = a.n_temps or {16: 15, 24: 27, 32: 43}.get(a.L, ladder.default_n_temps(a.L, 1 / T_MAX, 1 / T_MIN))
-    if a.replicas:
+    if a.equilibration:
+        print(json.dumps(equilibration(a.L, nt, a.equilibration, a.cycles, a.kappa)))
+    elif a.replicas:
         nts = [int(v) for v in a.replicas.split(",")]
         print(json.dumps(replicas(a.L, nts, nt, a.sets, a.cycles, a.burn, a.kappa)))
     else:
