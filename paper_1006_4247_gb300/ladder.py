@@ -43,7 +43,7 @@ DATA_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data")
 TRAIN_FILE = os.path.join(DATA_DIR, "ladder_train.npz")
 WEIGHTS_FILE = os.path.join(DATA_DIR, "ladder_net.npz")
 PAPER_WINDOW = (1 / 0.19, 1 / 0.12)  # Sec. 4: T from 0.12 to 0.19
-TRAIN_L = (4, 6, 8, 12, 16, 24)
+TRAIN_L = (4, 6, 8, 12, 16, 24, 32)
 TRAIN_WINDOWS = ((2.0, 8.0), (2.5, 8.0), PAPER_WINDOW, (3.0, 6.0), (4.0, 10.0), (1.5, 5.0))
 EPS_SAFETY = 0.9  # eps * max_x sum_6 |J| must stay below 1 (invertible cooling step)
 
@@ -296,8 +296,8 @@ def geometric_reference(L, J, beta_min, beta_max, n_temps, kappa):
 # ---------------------------------------------------------------- data set
 def training_rows(seed_base=5000):
     """The training cases: lattice sizes TRAIN_L, inverse-temperature windows
-    TRAIN_WINDOWS (three coupling samples each up to L = 16; at L = 24 one
-    sample of the paper's window and of [2, 8]), replica counts by
+    TRAIN_WINDOWS (three coupling samples each up to L = 16; at L = 24 and 32
+    one sample of the paper's window and of [2, 8]), replica counts by
     default_n_temps."""
     rows = []
     for L in TRAIN_L:

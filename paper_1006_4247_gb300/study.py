@@ -229,6 +229,45 @@ def equilibration(L=16, n_temps=15, n_runs=2000, cycles=1000, kappa=0.1, seed=85
     return out
 
 
+def learned_large(L=48, n_samples=32, n_run=8, cycles=300, burn=200, kappa=0.1, seed0=400):
+    """The learned ladder on a size far outside its training range (L = 48,
+    coupling seeds 400 + k): proposals for n_samples sets, and a short
+    acceptance comparison on n_run of them against the geometric ladder with
+    the paper's replica rule and one kappa.  The network picks N_T for the
+    geometric arm's measured worst-pair acceptance.  Round trips are not
+    measured (t_R at L = 48 is far beyond a short run)."""
+    J = [workloads.couplings(L, seed0 + k) for k in range(n_samples)]
+    bmin, bmax = 1 / T_MAX, 1 / T_MIN
+    nt_geo = ladder.default_n_temps(L, bmin, bmax)
+    geo = paper_ladder(nt_geo)
+    bound = min(ladder.eps_bound(L, j) for j in J[:n_run])
+    eps_geo = ladder.eps_from_kappa(geo, np.full(nt_geo - 1, kappa), bound)
+    acc_g, _, _ = run_method(L, J[:n_run], geo, "coolheat", eps_geo, cycles, burn, seed=17)
+    target = float(acc_g.min(1).mean())
+    net = ladder.LearnedLadder.load()
+    try:
+        lam = [net.predicted_length(L, j, bmin, bmax) for j in J]
+        auto = net.propose_many([(L, j, bmin, bmax) for j in J], target_acceptance=target)
+    finally:
+        net.close()
+    nts = [len(b) for b, _ in auto]
+    nt_l = max(nts[:n_run])  # one engine needs one N_T: the largest the net asks for among the runs
+    net = ladder.LearnedLadder.load()
+    try:
+        run = net.propose_many([(L, j, bmin, bmax) for j in J[:n_run]], n_temps=nt_l)
+    finally:
+        net.close()
+    acc_l, _, _ = run_method(L, J[:n_run], np.stack([b for b, _ in run]), "coolheat", np.stack([e for _, e in run]),
+                             cycles, burn, seed=17)
+    kap = [float(np.mean(e / np.diff(np.log(b)))) for b, e in run]
+    return {"L": L, "samples": n_samples, "run_samples": n_run, "cycles": cycles, "burn": burn,
+            "geometric": {"n_temps": nt_geo, "kappa": kappa, "acc_min": target, "acc_mean": float(acc_g.mean()),
+                          "acc_profile": acc_g.mean(0).round(4).tolist()},
+            "learned": {"n_temps_proposed": nts, "n_temps_run": nt_l, "predicted_Lambda": [round(x, 2) for x in lam],
+                        "kappa_mean": float(np.mean(kap)), "acc_min": float(acc_l.min(1).mean()),
+                        "acc_mean": float(acc_l.mean()), "acc_profile": acc_l.mean(0).round(4).tolist()}}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description="the paper's protocol on synthetic coupling sets")
     ap.add_argument("--L", type=int, default=16)
@@ -240,9 +279,12 @@ def main(argv=None):
     ap.add_argument("--methods", default="plain,decimation,coolheat")
     ap.add_argument("--replicas", default="", help="comma-separated N_T list: run the replica-count study")
     ap.add_argument("--equilibration", type=int, default=0, help="runs of the equilibration study (0: off)")
+    ap.add_argument("--learned-large", action="store_true", help="learned ladder at L (e.g. 48) vs geometric")
     a = ap.parse_args(argv)
     nt = a.n_temps or {16: 15, 24: 27, 32: 43}.get(a.L, ladder.default_n_temps(a.L, 1 / T_MAX, 1 / T_MIN))
-    if a.equilibration:
+    if a.learned_large:
+        print(json.dumps(learned_large(a.L, cycles=a.cycles, burn=a.burn)))
+    elif a.equilibration:
         print(json.dumps(equilibration(a.L, nt, a.equilibration, a.cycles, a.kappa)))
     elif a.replicas:
         nts = [int(v) for v in a.replicas.split(",")]

@@ -9,6 +9,8 @@ evaluated on held-out coupling samples at a lattice size it never saw
 * the judge: the geometric ladder with one cooling/heating parameter for
   all pairs, tuned by a scan on the evaluation samples themselves (the
   paper's procedure, Sec. 2.3), at the replica count of the paper's rule;
+* the same geometric ladder with epsilon tuned per pair and per sample from
+  that scan (no network: the ablation of the learned parameters);
 * the plain swap on the same geometric ladder (the standard method).
 
 All arms run as samples of one batched engine (cooling/heating exchange,
@@ -80,16 +82,23 @@ def test_learned_ladder_against_geometric(trained):
                       for i in range(len(lad.KAPPA_GRID))])
     kappa = lad.KAPPA_GRID[int(np.argmax(acc_k))]
     geo_min = float(np.mean([res[int(np.argmax(acc_k)) * N_SAMPLES + s][0].min() for s in range(N_SAMPLES)]))
+    # per-pair kappa of each sample from the same scan
+    per_pair = []
+    for k_, (L, J, _, _) in enumerate(samples):
+        acc_s = np.stack([res[i * N_SAMPLES + k_][0] for i in range(len(lad.KAPPA_GRID))])
+        kb, _ = lad.best_kappa(lad.KAPPA_GRID, acc_s)
+        per_pair.append(lad.eps_from_kappa(geo, kb, lad.eps_bound(L, J)))
 
     learned = net.propose_many(samples, n_temps=NT)
     auto = net.propose_many(samples, target_acceptance=geo_min)
     nt_small = int(round(0.7 * NT))
     small = net.propose_many(samples, n_temps=nt_small)
-    arms = {"geometric": [], "learned": [], "learned_auto": [], "learned_small": []}
+    arms = {"geometric": [], "geometric_per_pair": [], "learned": [], "learned_auto": [], "learned_small": []}
     cases = []
     for k, (L, J, _, _) in enumerate(samples):
         b, e = lad.geometric_reference(L, J, *WINDOW, NT, kappa)
         cases.append((L, J, b, e)); arms["geometric"].append(len(cases) - 1)
+        cases.append((L, J, geo, per_pair[k])); arms["geometric_per_pair"].append(len(cases) - 1)
         cases.append((L, J, *learned[k])); arms["learned"].append(len(cases) - 1)
         cases.append((L, J, *auto[k])); arms["learned_auto"].append(len(cases) - 1)
         cases.append((L, J, *small[k])); arms["learned_small"].append(len(cases) - 1)
@@ -98,7 +107,7 @@ def test_learned_ladder_against_geometric(trained):
                             CYCLES, BURN, seed=43, mode="plain")
     out = {name: _summary([res[i] for i in idx]) for name, idx in arms.items()}
     out["plain_geometric"] = _summary(plain)
-    out["n_temps"] = {"geometric": NT, "learned": NT, "learned_auto": [len(a[0]) for a in auto],
+    out["n_temps"] = {"geometric": NT, "geometric_per_pair": NT, "learned": NT, "learned_auto": [len(a[0]) for a in auto],
                       "learned_small": nt_small, "plain_geometric": NT}
     out["kappa_scan"] = {"grid": list(lad.KAPPA_GRID), "acc_mean": acc_k.round(4).tolist(), "chosen": kappa}
     out["learned_kappa"] = [float(np.mean(e / np.diff(np.log(b)))) for b, e in learned]
