@@ -363,7 +363,14 @@ def ours(args):
                 "kernel": "k_resident / k_resident_cl (sweep block in shared memory, one CTA or a cluster)",
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz",
                 "alg_flops_per_launch": upd * 60.0 / n_launch, "avg_launch_us": t / n_launch * 1e6,
-                "effective_hbm_GBps": upd * 36.4 / t / 1e9}
+                "effective_hbm_GBps": upd * 36.4 / t / 1e9,
+                # the resident blocks' actual limit: the SM's shared-memory data path. Per 4-site
+                # vector an overrelaxation update issues 24 16-byte loads (own spins 3, neighbour
+                # rows 15, couplings 6) and 3 16-byte stores: 108 B per site update.
+                "onchip": {"bound": "shared-memory data path", "achieved": upd * 108.0 / t / 1e12,
+                           "peak": 152 * 128 * 2.07e9 / 1e12, "unit": "TB/s",
+                           "frac": upd * 108.0 / t / (152 * 128 * 2.07e9),
+                           "peak_source": "derived: 152 SMs x 128 B/clock x 2.07 GHz"}}
 
     dominant = max(("or", "resident"), key=lambda k: prof_ms.get(k, 0.0))
     share = {k: v / max(sum(prof_ms.values()), 1e-9) for k, v in prof_ms.items()}
