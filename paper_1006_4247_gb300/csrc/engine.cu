@@ -593,6 +593,21 @@ pt_status create_impl(pt_handle* out, int n_samples, const int* Ls, const int* N
     }
     d.max_half = 0;
     for (const SampleDesc& sd : e->samples) d.max_half = std::max(d.max_half, sd.half);
+    // the staged cooling/heating exchange keeps the heated proposal of every
+    // pair (one configuration each) between its two kernels
+    d.heat_buf = nullptr;
+    d.heat_H = d.heat_lnJ = nullptr;
+    if (exchange_smem_supported(2, d.max_half, e->fp64) && e->P > 0) {
+        const size_t n = (size_t)e->P * 6 * (size_t)d.max_half;
+        st = e->dalloc(&d.heat_buf, n * e->esz());
+        if (st == PT_OK) st = e->dalloc((void**)&d.heat_H, sizeof(double) * (size_t)e->P);
+        if (st == PT_OK) st = e->dalloc((void**)&d.heat_lnJ, sizeof(double) * (size_t)e->P);
+        if (st != PT_OK) {
+            e->release();
+            delete e;
+            return st;
+        }
+    }
 
     st = rebuild_lists(e);
     if (st == PT_OK)
@@ -773,7 +788,8 @@ static pt_status exchange_impl(pt_engine* e, pt_mode mode, const float* eps) {
         pt_status st = compute_energy(e);
         if (st != PT_OK) return st;
     }
-    RUN(PT_KERNEL_EXCHANGE, 1, launch_exchange(e->d, e->fp64, (int)mode, e->stream));
+    RUN(PT_KERNEL_EXCHANGE, exchange_launch_count(e->d, e->fp64, (int)mode),
+        launch_exchange(e->d, e->fp64, (int)mode, e->stream));
     RUN(PT_KERNEL_OTHER, 1, launch_advance_step(e->d, 1, e->stream));
     e->step_host += 1;
     return PT_OK;

@@ -400,6 +400,12 @@ static cudaError_t launch_cluster(K kernel, const DevBatch& b, int cs, cudaStrea
     return cudaLaunchKernelEx(&cfg, kernel, b);
 }
 
+int exchange_launch_count(const DevBatch& b, bool fp64, int mode) {
+    // the staged cooling/heating runs the heating pre-pass first
+    if (mode == 2 && b.exchange_impl != 1 && exchange_smem_supported(mode, b.max_half, fp64)) return 2;
+    return 1;
+}
+
 cudaError_t launch_exchange(const DevBatch& b, bool fp64, int mode, cudaStream_t st) {
     if (mode == 0) {
         k_exchange_plain<<<b.n_chains, 32, 0, st>>>(b);

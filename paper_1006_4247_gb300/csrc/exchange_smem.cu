@@ -82,69 +82,93 @@ __device__ __forceinline__ T sx_decim_D(T n, T b1, T b2, T db, T lr) {
     return ln_sinhc<T>(R2) - ln_sinhc<T>(R1);
 }
 
-// One pass of the cooling sweep of s1 and the heating sweep of s2 over V-site
-// vectors (16- or 8-byte shared-memory loads of the neighbour rows).  Pass 0
-// cools colour 0 of s1 (field from colour 1 of s1) into f1 and heats colour 1
-// of s2 (field from colour 0 of s2) into f2; pass 1 cools colour 1 (field
-// from the cooled colour 0 in f1) and heats colour 0 (field from the heated
-// colour 1 in f2), and sums the energies of the two transforms.
-template <typename T, int V>
-__device__ __forceinline__ void ch_pass(const SampleDesc& sd, const T* s1, const T* s2, T* f1, T* f2,
-                                        const float* J0, const float* J1, T eps, int pass, T& lj1, T& lj2, T& hc,
-                                        T& hh) {
+// ---------------------------------------------------------------------------
+// Cooling/heating (section III.B).  The heated proposal of pair i is
+// C^-1 of the configuration at beta_{i+1}, which no earlier pair of the update
+// touches: k_heat_pre computes it for every pair of every chain at once (with
+// its energy and ln det J_C), and k_exchange_coolheat_smem then walks the
+// pairs of each chain in order, cooling the configuration at beta_i (which
+// does depend on the earlier decisions) in shared memory.
+// ---------------------------------------------------------------------------
+constexpr int HP_THREADS = 512;
+
+// One colour of the cooling (COOL) or heating sweep of a configuration held
+// in shared memory, over V-site vectors: the sites of colour `col` of `src`
+// are transformed into `dst` (dst may equal src), the field coming from the
+// other colour of `field`.  Adds ln det J_f to lj and, with ENERGY, -s.S of
+// the new spins to e.
+template <typename T, int V, bool COOL, bool ENERGY>
+__device__ __forceinline__ void ch_colour(const SampleDesc& sd, const T* field, const T* src, T* dst,
+                                          const float* J0, const float* J1, int col, T eps, T& lj, T& e) {
     const int half = sd.half;
-    const int cc = pass, hcol = 1 - pass;  // colour cooled, colour heated
-    const T* cfield = pass == 0 ? s1 + 3 * half : f1;
-    const T* hfield = pass == 0 ? s2 : f2 + 3 * half;
-    const float* Jc_own = cc ? J1 : J0;
-    const float* Jc_oth = cc ? J0 : J1;
-    const float* Jh_own = hcol ? J1 : J0;
-    const float* Jh_oth = hcol ? J0 : J1;
+    const T* fo = field + (1 - col) * 3 * half;
+    const float* Jown = col ? J1 : J0;
+    const float* Joth = col ? J0 : J1;
     for (int h0 = (int)threadIdx.x * V; h0 < half; h0 += (int)blockDim.x * V) {
-        {
-            const VRow q = vrow<V>(sd, cc, h0);
-            T S[3][V], s[3][V];
-            nbr_field<T, V>(cfield, Jc_own, Jc_oth, half, h0, q.xs, q.hyp, q.hym, q.hzp, q.hzm, q.p, S);
+        const VRow q = vrow<V>(sd, col, h0);
+        T S[3][V], s[3][V];
+        nbr_field<T, V>(fo, Jown, Joth, half, h0, q.xs, q.hyp, q.hym, q.hzp, q.hzm, q.p, S);
 #pragma unroll
-            for (int c = 0; c < 3; ++c) ldv<T, V>(s1 + cc * 3 * half + c * half + h0, s[c]);
+        for (int c = 0; c < 3; ++c) ldv<T, V>(src + col * 3 * half + c * half + h0, s[c]);
 #pragma unroll
-            for (int v = 0; v < V; ++v) {
-                const V3<T> Sv = {S[0][v], S[1][v], S[2][v]};
-                V3<T> sv = {s[0][v], s[1][v], s[2][v]};
-                lj1 += cool_site<T>(eps, Sv, sv);
-                if (pass == 1) hc -= dot(sv, Sv);
-                s[0][v] = sv.x; s[1][v] = sv.y; s[2][v] = sv.z;
-            }
-#pragma unroll
-            for (int c = 0; c < 3; ++c) stv<T, V>(f1 + cc * 3 * half + c * half + h0, s[c]);
+        for (int v = 0; v < V; ++v) {
+            const V3<T> Sv = {S[0][v], S[1][v], S[2][v]};
+            V3<T> sv = {s[0][v], s[1][v], s[2][v]};
+            lj += COOL ? cool_site<T>(eps, Sv, sv) : heat_site<T>(eps, Sv, sv);
+            if (ENERGY) e -= dot(sv, Sv);
+            s[0][v] = sv.x; s[1][v] = sv.y; s[2][v] = sv.z;
         }
-        {
-            const VRow q = vrow<V>(sd, hcol, h0);
-            T S[3][V], u[3][V];
-            nbr_field<T, V>(hfield, Jh_own, Jh_oth, half, h0, q.xs, q.hyp, q.hym, q.hzp, q.hzm, q.p, S);
 #pragma unroll
-            for (int c = 0; c < 3; ++c) ldv<T, V>(s2 + hcol * 3 * half + c * half + h0, u[c]);
-#pragma unroll
-            for (int v = 0; v < V; ++v) {
-                const V3<T> Sv = {S[0][v], S[1][v], S[2][v]};
-                V3<T> uv = {u[0][v], u[1][v], u[2][v]};
-                lj2 += heat_site<T>(eps, Sv, uv);
-                if (pass == 1) hh -= dot(uv, Sv);
-                u[0][v] = uv.x; u[1][v] = uv.y; u[2][v] = uv.z;
-            }
-#pragma unroll
-            for (int c = 0; c < 3; ++c) stv<T, V>(f2 + hcol * 3 * half + c * half + h0, u[c]);
-        }
+        for (int c = 0; c < 3; ++c) stv<T, V>(dst + col * 3 * half + c * half + h0, s[c]);
     }
 }
 
-// ---------------------------------------------------------------------------
-// Cooling/heating: slots hold s1 (now at beta_i), s2 (at beta_{i+1}) and the
-// transforms f1 = C(s1), f2 = C^-1(s2).  Accept: f2 is final at beta_i and is
-// written into s1's buffer; f1 moves on as the next s1 and will be written
-// into s2's buffer.  Reject: s1 is final (written back if it was transformed
-// earlier in this update); s2 moves on.
-// ---------------------------------------------------------------------------
+// Heated proposal of pair i (blockIdx.y) of chain blockIdx.x: C^-1 = colour
+// 1 then colour 0 of the inverse step, in place in shared memory, on the
+// configuration at beta_{i+1}, with eps_i.
+template <typename T>
+__global__ void __launch_bounds__(HP_THREADS) k_heat_pre(DevBatch a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[2 * 32];
+    const int ch = blockIdx.x, i = blockIdx.y;
+    const ChainDesc cd = a.chains[ch];
+    const SampleDesc& sd = a.samples[cd.s];
+    if (i + 1 >= sd.NT) return;  // uniform over the block
+    const int half = sd.half, n3 = 6 * half;
+    T* cfg = reinterpret_cast<T*>(smem_raw);
+    const T* pool = (const T*)a.spins + a.chain_off[ch];
+    sx_copy(cfg, pool + (long long)a.bufmap[cd.r0 + i + 1] * n3, n3);
+    __syncthreads();
+    const float* J0 = a.J + sd.J_off;
+    const float* J1 = a.J + sd.J_off + 3 * half;
+    const T eps = (T)a.eps[sd.eps_off + i];
+    T part[2] = {(T)0, (T)0};  // ln det J_C, energy
+    T none = (T)0;
+    const bool v2 = (sd.hL % 2) == 0;
+    if (v2) ch_colour<T, 2, false, false>(sd, cfg, cfg, cfg, J0, J1, 1, eps, part[0], none);
+    else ch_colour<T, 1, false, false>(sd, cfg, cfg, cfg, J0, J1, 1, eps, part[0], none);
+    __syncthreads();
+    if (v2) ch_colour<T, 2, false, true>(sd, cfg, cfg, cfg, J0, J1, 0, eps, part[0], part[1]);
+    else ch_colour<T, 1, false, true>(sd, cfg, cfg, cfg, J0, J1, 0, eps, part[0], part[1]);
+    __syncthreads();
+    const long long pair = cd.pair_off + i;
+    T* out = (T*)a.heat_buf + pair * (6LL * a.max_half);
+    sx_copy(out, cfg, n3);
+    double tot[2];
+    block_sum_multi<T, 2>(part, tot, red);
+    if (threadIdx.x == 0) {
+        a.heat_lnJ[pair] = tot[0];
+        a.heat_H[pair] = tot[1];
+    }
+}
+
+// The pair walk of one chain.  Slot A holds s1 (the configuration now at
+// beta_i), slot F receives f1 = C(s1).  Accept: the heated configuration of
+// beta_{i+1} is final at beta_i and is copied into s1's buffer; f1 moves on
+// as the next s1 (to be written into s2's buffer).  Reject: s1 is final
+// (written back if it was transformed earlier in this update) and s2 is
+// loaded as the next s1.  Buffer identities never change; only contents,
+// labels and energies do.
 template <typename T>
 __global__ void __launch_bounds__(SX_THREADS, 1) k_exchange_coolheat_smem(DevBatch a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -161,32 +185,31 @@ __global__ void __launch_bounds__(SX_THREADS, 1) k_exchange_coolheat_smem(DevBat
     const float* J1 = a.J + sd.J_off + 3 * half;
     const unsigned long long step = *a.d_step;
     const double* beta = a.betas + sd.beta_off;
-    int A = 0;                      // slot of s1
-    int ownerA = sm.buf[0];         // global buffer of s1
+    const bool v2 = (sd.hL % 2) == 0;
+    int A = 0;               // slot of s1
+    int ownerA = sm.buf[0];  // global buffer of s1
     bool dirtyA = false;
     sx_copy(slot(A), pool + (long long)ownerA * n3, n3);
+    __syncthreads();
     for (int i = 0; i + 1 < NT; ++i) {
-        const int B = (A + 1) & 3, F1 = (A + 2) & 3, F2 = (A + 3) & 3;
+        const int F = 1 - A;
         const int ownerB = sm.buf[i + 1];
-        sx_copy(slot(B), pool + (long long)ownerB * n3, n3);
-        __syncthreads();
         const T eps = (T)a.eps[sd.eps_off + i];
         const T* s1 = slot(A);
-        const T* s2 = slot(B);
-        T* f1 = slot(F1);
-        T* f2 = slot(F2);
-        T lj1 = (T)0, lj2 = (T)0, hc = (T)0, hh = (T)0;  // per-thread partials of a few sites
-        const bool v2 = (sd.hL % 2) == 0;  // 2-site vectors where the row length allows
-        if (v2) ch_pass<T, 2>(sd, s1, s2, f1, f2, J0, J1, eps, 0, lj1, lj2, hc, hh);
-        else ch_pass<T, 1>(sd, s1, s2, f1, f2, J0, J1, eps, 0, lj1, lj2, hc, hh);
+        T* f1 = slot(F);
+        T part[2] = {(T)0, (T)0};  // ln det J_C(s1), energy of C(s1)
+        T none = (T)0;
+        if (v2) ch_colour<T, 2, true, false>(sd, s1, s1, f1, J0, J1, 0, eps, part[0], none);
+        else ch_colour<T, 1, true, false>(sd, s1, s1, f1, J0, J1, 0, eps, part[0], none);
         __syncthreads();
-        if (v2) ch_pass<T, 2>(sd, s1, s2, f1, f2, J0, J1, eps, 1, lj1, lj2, hc, hh);
-        else ch_pass<T, 1>(sd, s1, s2, f1, f2, J0, J1, eps, 1, lj1, lj2, hc, hh);
-        const T part[4] = {lj1, lj2, hc, hh};
-        double tot[4];
-        block_sum_multi<T, 4>(part, tot, sm.red);
-        const double LJ1 = tot[0], LJ2 = tot[1], HC = tot[2], HH = tot[3];
+        if (v2) ch_colour<T, 2, true, true>(sd, f1, s1, f1, J0, J1, 1, eps, part[0], part[1]);
+        else ch_colour<T, 1, true, true>(sd, f1, s1, f1, J0, J1, 1, eps, part[0], part[1]);
+        double tot[2];
+        block_sum_multi<T, 2>(part, tot, sm.red);
+        const long long pair = cd.pair_off + i;
         if (threadIdx.x == 0) {
+            const double LJ1 = tot[0], HC = tot[1];
+            const double HH = a.heat_H[pair], LJ2 = a.heat_lnJ[pair];
             const double b1 = beta[i], b2 = beta[i + 1];
             const double lnA = -b2 * HC - b1 * HH + b1 * sm.H[i] + b2 * sm.H[i + 1] + LJ1 - LJ2;
             const uint4 w = rng_words(a.seed, (uint32_t)cd.s, (uint32_t)i, (uint32_t)cd.copy, step, 1u);
@@ -195,8 +218,6 @@ __global__ void __launch_bounds__(SX_THREADS, 1) k_exchange_coolheat_smem(DevBat
             sm.flag = ok;
             if (ok) {
                 a.acc[cd.pair_off + i] += 1;
-                sm.buf[i] = ownerA;       // C^-1(s2) goes into s1's old buffer
-                sm.buf[i + 1] = ownerB;   // C(s1) will go into s2's old buffer
                 sm.H[i] = HH;
                 sm.H[i + 1] = HC;
                 const int t = sm.lab[i]; sm.lab[i] = sm.lab[i + 1]; sm.lab[i + 1] = t;
@@ -204,16 +225,18 @@ __global__ void __launch_bounds__(SX_THREADS, 1) k_exchange_coolheat_smem(DevBat
         }
         __syncthreads();
         if (sm.flag) {
-            sx_copy(pool + (long long)ownerA * n3, f2, n3);
-            A = F1;
-            ownerA = ownerB;
+            // C^-1(s2) is final at beta_i: into s1's buffer; C(s1) moves on
+            sx_copy(pool + (long long)ownerA * n3, (const T*)a.heat_buf + pair * (6LL * a.max_half), n3);
+            A = F;
             dirtyA = true;
         } else {
+            // s1 is final at beta_i; s2 moves on
             if (dirtyA) sx_copy(pool + (long long)ownerA * n3, slot(A), n3);
-            A = B;
-            ownerA = ownerB;
+            sx_copy(slot(F), pool + (long long)ownerB * n3, n3);
+            A = F;
             dirtyA = false;
         }
+        ownerA = ownerB;
         __syncthreads();
     }
     if (dirtyA) sx_copy(pool + (long long)ownerA * n3, slot(A), n3);
@@ -323,9 +346,8 @@ __global__ void __launch_bounds__(SX_THREADS, 1) k_exchange_decimation_smem(DevB
     sx_store_state(a, cd, NT, sm, ch);
 }
 
-size_t exchange_smem_bytes(int mode, int half, bool fp64) {
-    return (size_t)(mode == 2 ? 4 : 2) * 6 * half * (fp64 ? 8 : 4);
-}
+// Two slots of one configuration each (s1 and its transform, or the pair).
+size_t exchange_smem_bytes(int mode, int half, bool fp64) { return (size_t)2 * 6 * half * (fp64 ? 8 : 4); }
 
 bool exchange_smem_supported(int mode, int max_half, bool fp64) {
     return (mode == 1 || mode == 2) && exchange_smem_bytes(mode, max_half, fp64) <= 200 * 1024;
@@ -335,11 +357,20 @@ cudaError_t launch_exchange_smem(const DevBatch& b, bool fp64, int mode, int max
     const size_t smem = exchange_smem_bytes(mode, max_half, fp64);
     cudaError_t e;
     if (mode == 2) {
+        if (!b.heat_buf) return cudaErrorInvalidValue;  // the engine allocates it whenever this path exists
+        const size_t one = smem / 2;                     // the pre-pass holds one configuration
+        const dim3 grid_pre((unsigned)b.n_chains, (unsigned)(b.max_NT - 1), 1);
         if (fp64) {
+            e = ensure_smem((const void*)k_heat_pre<double>, one);
+            if (e != cudaSuccess) return e;
+            k_heat_pre<double><<<grid_pre, HP_THREADS, one, st>>>(b);
             e = ensure_smem((const void*)k_exchange_coolheat_smem<double>, smem);
             if (e != cudaSuccess) return e;
             k_exchange_coolheat_smem<double><<<b.n_chains, SX_THREADS, smem, st>>>(b);
         } else {
+            e = ensure_smem((const void*)k_heat_pre<float>, one);
+            if (e != cudaSuccess) return e;
+            k_heat_pre<float><<<grid_pre, HP_THREADS, one, st>>>(b);
             e = ensure_smem((const void*)k_exchange_coolheat_smem<float>, smem);
             if (e != cudaSuccess) return e;
             k_exchange_coolheat_smem<float><<<b.n_chains, SX_THREADS, smem, st>>>(b);

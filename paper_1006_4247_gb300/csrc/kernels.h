@@ -58,6 +58,13 @@ struct DevBatch {
     // resident replicas grouped by CTAs per replica (1, 2, 4, 8): slices of
     // res_reps and the largest L^3/2 of each group
     int rcl_begin[4], rcl_count[4], rcl_half[4];
+    // cooling/heating with the pair staged in shared memory: the heated
+    // configuration of every pair (pair index x 6 max_half elements), its
+    // energy and ln det J_C, computed before the pairs are walked (NULL when
+    // that exchange is not available to the batch)
+    void* heat_buf;
+    double* heat_H;
+    double* heat_lnJ;
 };
 
 // Record the text returned by pt_last_error() for the calling thread.
@@ -82,6 +89,8 @@ cudaError_t launch_init_spins(const DevBatch& b, bool fp64, int ordered, cudaStr
 cudaError_t launch_advance_step(const DevBatch& b, int by, cudaStream_t st);
 cudaError_t launch_overlap(const DevBatch& b, bool fp64, cudaStream_t st);
 cudaError_t launch_exchange(const DevBatch& b, bool fp64, int mode, cudaStream_t st);
+// Kernels one tempering update launches.
+int exchange_launch_count(const DevBatch& b, bool fp64, int mode);
 
 // Decimation / cooling-heating exchanges with the pair staged in shared
 // memory (one CTA per chain), for configurations that fit on one SM.
