@@ -90,7 +90,7 @@ __device__ __forceinline__ T sx_decim_D(T n, T b1, T b2, T db, T lr) {
 // pairs of each chain in order, cooling the configuration at beta_i (which
 // does depend on the earlier decisions) in shared memory.
 // ---------------------------------------------------------------------------
-constexpr int HP_THREADS = 512;
+constexpr int HP_THREADS = 256;
 
 // One colour of the cooling (COOL) or heating sweep of a configuration held
 // in shared memory, over V-site vectors: the sites of colour `col` of `src`
@@ -124,36 +124,32 @@ __device__ __forceinline__ void ch_colour(const SampleDesc& sd, const T* field, 
 }
 
 // Heated proposal of pair i (blockIdx.y) of chain blockIdx.x: C^-1 = colour
-// 1 then colour 0 of the inverse step, in place in shared memory, on the
-// configuration at beta_{i+1}, with eps_i.
+// 1 then colour 0 of the inverse step on the configuration at beta_{i+1},
+// with eps_i, read from the pool and written straight to the proposal buffer
+// (the second colour's field is the first colour's output, visible to the
+// block after the barrier).
 template <typename T>
 __global__ void __launch_bounds__(HP_THREADS) k_heat_pre(DevBatch a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[2 * 32];
     const int ch = blockIdx.x, i = blockIdx.y;
     const ChainDesc cd = a.chains[ch];
     const SampleDesc& sd = a.samples[cd.s];
     if (i + 1 >= sd.NT) return;  // uniform over the block
     const int half = sd.half, n3 = 6 * half;
-    T* cfg = reinterpret_cast<T*>(smem_raw);
-    const T* pool = (const T*)a.spins + a.chain_off[ch];
-    sx_copy(cfg, pool + (long long)a.bufmap[cd.r0 + i + 1] * n3, n3);
-    __syncthreads();
+    const T* src = (const T*)a.spins + a.chain_off[ch] + (long long)a.bufmap[cd.r0 + i + 1] * n3;
+    const long long pair = cd.pair_off + i;
+    T* out = (T*)a.heat_buf + pair * (6LL * a.max_half);
     const float* J0 = a.J + sd.J_off;
     const float* J1 = a.J + sd.J_off + 3 * half;
     const T eps = (T)a.eps[sd.eps_off + i];
     T part[2] = {(T)0, (T)0};  // ln det J_C, energy
     T none = (T)0;
     const bool v2 = (sd.hL % 2) == 0;
-    if (v2) ch_colour<T, 2, false, false>(sd, cfg, cfg, cfg, J0, J1, 1, eps, part[0], none);
-    else ch_colour<T, 1, false, false>(sd, cfg, cfg, cfg, J0, J1, 1, eps, part[0], none);
+    if (v2) ch_colour<T, 2, false, false>(sd, src, src, out, J0, J1, 1, eps, part[0], none);
+    else ch_colour<T, 1, false, false>(sd, src, src, out, J0, J1, 1, eps, part[0], none);
     __syncthreads();
-    if (v2) ch_colour<T, 2, false, true>(sd, cfg, cfg, cfg, J0, J1, 0, eps, part[0], part[1]);
-    else ch_colour<T, 1, false, true>(sd, cfg, cfg, cfg, J0, J1, 0, eps, part[0], part[1]);
-    __syncthreads();
-    const long long pair = cd.pair_off + i;
-    T* out = (T*)a.heat_buf + pair * (6LL * a.max_half);
-    sx_copy(out, cfg, n3);
+    if (v2) ch_colour<T, 2, false, true>(sd, out, src, out, J0, J1, 0, eps, part[0], part[1]);
+    else ch_colour<T, 1, false, true>(sd, out, src, out, J0, J1, 0, eps, part[0], part[1]);
     double tot[2];
     block_sum_multi<T, 2>(part, tot, red);
     if (threadIdx.x == 0) {
@@ -358,19 +354,14 @@ cudaError_t launch_exchange_smem(const DevBatch& b, bool fp64, int mode, int max
     cudaError_t e;
     if (mode == 2) {
         if (!b.heat_buf) return cudaErrorInvalidValue;  // the engine allocates it whenever this path exists
-        const size_t one = smem / 2;                     // the pre-pass holds one configuration
         const dim3 grid_pre((unsigned)b.n_chains, (unsigned)(b.max_NT - 1), 1);
         if (fp64) {
-            e = ensure_smem((const void*)k_heat_pre<double>, one);
-            if (e != cudaSuccess) return e;
-            k_heat_pre<double><<<grid_pre, HP_THREADS, one, st>>>(b);
+            k_heat_pre<double><<<grid_pre, HP_THREADS, 0, st>>>(b);
             e = ensure_smem((const void*)k_exchange_coolheat_smem<double>, smem);
             if (e != cudaSuccess) return e;
             k_exchange_coolheat_smem<double><<<b.n_chains, SX_THREADS, smem, st>>>(b);
         } else {
-            e = ensure_smem((const void*)k_heat_pre<float>, one);
-            if (e != cudaSuccess) return e;
-            k_heat_pre<float><<<grid_pre, HP_THREADS, one, st>>>(b);
+            k_heat_pre<float><<<grid_pre, HP_THREADS, 0, st>>>(b);
             e = ensure_smem((const void*)k_exchange_coolheat_smem<float>, smem);
             if (e != cudaSuccess) return e;
             k_exchange_coolheat_smem<float><<<b.n_chains, SX_THREADS, smem, st>>>(b);
