@@ -137,12 +137,15 @@ template <> struct MX<float> {
     static __device__ __forceinline__ float sin_(float x) { return __sinf(x); }
     static __device__ __forceinline__ float cos_(float x) { return __cosf(x); }
     static __device__ __forceinline__ float log_(float x) { return __logf(x); }
+    // hardware reciprocal quotient (2 ulp); operands here are O(1) or small angles
+    static __device__ __forceinline__ float div_(float a, float b) { return __fdividef(a, b); }
 };
 template <> struct MX<double> {
     static __device__ __forceinline__ void sincos_(double x, double* s, double* c) { sincos(x, s, c); }
     static __device__ __forceinline__ double sin_(double x) { return sin(x); }
     static __device__ __forceinline__ double cos_(double x) { return cos(x); }
     static __device__ __forceinline__ double log_(double x) { return log(x); }
+    static __device__ __forceinline__ double div_(double a, double b) { return a / b; }
 };
 
 template <typename T> struct V3 { T x, y, z; };
@@ -275,7 +278,7 @@ __device__ __forceinline__ T ln_sinhc(T R) {
 }
 
 template <typename T>
-__device__ __forceinline__ T sinc_(T a) { return a == (T)0 ? (T)1 : MX<T>::sin_(a) / a; }
+__device__ __forceinline__ T sinc_(T a) { return a == (T)0 ? (T)1 : MX<T>::div_(MX<T>::sin_(a), a); }
 
 // Cooling step (section III.B): rotate s towards S by alpha = eps |p|,
 // p = S - (S.s) s; returns ln det J_f = ln[(1 - eps S.s)(cos a - eps S.s sinc a)].
@@ -311,7 +314,7 @@ __device__ __forceinline__ T heat_site(T eps, const V3<T>& S, V3<T>& s) {
     const V3<T> p = {S.x - sS * s.x, S.y - sS * s.y, S.z - sS * s.z};
     const T pn = M<T>::sqrt_(dot(p, p));
     const T e = eps * nS;
-    const T inv = nS > (T)0 ? (T)1 / nS : (T)0;
+    const T inv = nS > (T)0 ? MX<T>::div_((T)1, nS) : (T)0;
     const T cp = nS > (T)0 ? sS * inv : (T)1;  // cos(theta')
     const T sp = pn * inv;                     // sin(theta')
     T alpha = e * sp, sa, ca;
@@ -319,20 +322,20 @@ __device__ __forceinline__ T heat_site(T eps, const V3<T>& S, V3<T>& s) {
     for (int it = 0; it < M<T>::newton_max; ++it) {
         // f = alpha - e sin(theta' + alpha), f' = 1 - e cos(theta' + alpha)
         const T sth = sp * ca + cp * sa, cth = cp * ca - sp * sa;
-        const T d = (alpha - e * sth) / ((T)1 - e * cth);
+        const T d = MX<T>::div_(alpha - e * sth, (T)1 - e * cth);  // only the path to the root
         alpha -= d;
         MX<T>::sincos_(alpha, &sa, &ca);
         if (fabs(d) < M<T>::newton_tol) break;
     }
     if (pn > (T)0) {
-        const T f = sa / pn;
+        const T f = MX<T>::div_(sa, pn);
         s.x = s.x * ca - p.x * f;
         s.y = s.y * ca - p.y * f;
         s.z = s.z * ca - p.z * f;
         renorm(s);
     }
     const T cth = cp * ca - sp * sa;  // cos(theta)
-    const T sinc = alpha == (T)0 ? (T)1 : sa / alpha;
+    const T sinc = alpha == (T)0 ? (T)1 : MX<T>::div_(sa, alpha);
     const T j = ((T)1 - e * cth) * (ca - e * cth * sinc);
     return MX<T>::log_(fabs(j));
 }
