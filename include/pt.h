@@ -219,14 +219,31 @@ pt_status pt_profile_read(pt_handle h, double *ms, int64_t *launches);
 
 /* Choose how pt_sweep runs the local updates.
  *   PT_POLICY_AUTO (default): shared-memory resident sweep blocks when every
- *     sample's replica fits (float: L/2 divisible by 4 and at most 100 KB of
- *     spins per replica, e.g. L = 8, 16; double: L/2 even, at most 100 KB),
- *     else streaming half sweeps;
+ *     sample's replica fits one CTA or a cluster of 2, 4 or 8 CTAs (float: L/2
+ *     a multiple of 2 or 4; double: L/2 even; spins and couplings of a replica,
+ *     or of its z-slab, at most 200 KB per CTA: float up to L = 16 on one CTA,
+ *     L = 24 and 32 on clusters), else streaming half sweeps;
  *   PT_POLICY_STREAMING: one kernel per half sweep over HBM;
  *   PT_POLICY_RESIDENT: resident blocks; PT_ERR_STATE if a sample does not fit.
  * Both give the same chain (same updates, same random numbers). */
 typedef enum { PT_POLICY_AUTO = 0, PT_POLICY_STREAMING = 1, PT_POLICY_RESIDENT = 2 } pt_policy;
 pt_status pt_set_policy(pt_handle h, int policy);
+
+/* Bounded device-side waits and a hook to test their failure path.
+ * The only kernel that waits on the device is the bulk-copy (TMA) half sweep
+ * of overrelaxation (selected by PT_TMA=1 in the environment when the handle
+ * is created; FP32, every L a multiple of 8, streaming policy): each of its
+ * mbarrier waits polls at most `limit` times (0 restores the default, 2^22),
+ * then sets the handle's device error word, lets the copies it has in flight
+ * land and returns; the next call that synchronises (pt_measure, pt_get_spins,
+ * pt_get_stats, ...) returns PT_ERR_TIMEOUT once and clears the word.  The
+ * spins of the half sweep that gave up are left partly updated (each still a
+ * valid unit vector); the handle stays usable.
+ * inject != 0 makes every later launch of that kernel leave the copies of one
+ * stage un-issued (first replica of the first work item of CTA 0), so the wait
+ * for it runs out; inject = 0 turns that off.  PT_ERR_STATE if inject != 0 and
+ * the handle does not use the bulk-copy half sweep. */
+pt_status pt_set_wait_limit(pt_handle h, unsigned long long limit, int inject);
 
 /* Energies H = -sum_<xy> J_xy s_x . s_y of configurations that live in the
  * caller's own device memory, computed without allocating any memory.

@@ -557,6 +557,8 @@ pt_status create_impl(pt_handle* out, int n_samples, const int* Ls, const int* N
     TRY(upload(e, &d.d_step, z1));
     std::vector<int> zerr(1, 0);
     TRY(upload(e, &d.err, zerr));
+    d.wait_limit = WAIT_LIMIT_DEFAULT;
+    d.wait_fault = 0;
     int4* dTI; TRY(upload(e, &dTI, e->tma_items)); d.tma_items = dTI;
     d.n_tma_items = (int)e->tma_items.size();
     std::vector<double> zt(e->tile_cap, 0.0), zq((size_t)e->sumNT * 9, 0.0), zx((size_t)e->sumNT, 0.0);
@@ -846,7 +848,7 @@ pt_status pt_cycles(pt_handle e, int n_cycles, int n_hb, int n_or, const int* n_
         CK(cudaStreamSynchronize(e->stream));
     }
     std::vector<long long> key = {n_hb, mx, n_or_samples ? 1 : 0, (long long)mode, measure, e->policy, e->T,
-                                  (long long)e->res_reps.size()};
+                                  (long long)e->res_reps.size(), (long long)e->d.wait_limit, e->d.wait_fault};
     if (n_or_samples) key.insert(key.end(), n_or_samples, n_or_samples + e->S);
     if (!e->graph_exec || key != e->graph_key) {
         if (e->graph_exec) cudaGraphExecDestroy(e->graph_exec);
@@ -1247,6 +1249,17 @@ pt_status pt_set_policy(pt_handle e, int policy) {
     e->policy = policy;
     choose_paths(e);
     return rebuild_lists(e);
+}
+
+pt_status pt_set_wait_limit(pt_handle e, unsigned long long limit, int inject) {
+    if (!e) return fail(PT_ERR_ARG, "NULL handle");
+    if (inject && (!e->all_tma || e->tma_items.empty()))
+        return fail(PT_ERR_STATE, "the batch does not use the bulk-copy half sweep");
+    pt_status st = sync(e);
+    if (st != PT_OK) return st;
+    e->d.wait_limit = limit ? limit : WAIT_LIMIT_DEFAULT;
+    e->d.wait_fault = inject ? 1 : 0;
+    return PT_OK;
 }
 
 pt_status pt_destroy(pt_handle e) {

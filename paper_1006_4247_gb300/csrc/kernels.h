@@ -7,6 +7,10 @@
 
 namespace ptk {
 
+// Polls of a bounded mbarrier wait before it gives up (the default of
+// DevBatch::wait_limit, and the least the drain after a failed wait uses).
+constexpr unsigned long long WAIT_LIMIT_DEFAULT = 1ull << 22;
+
 // Raise a kernel's dynamic shared-memory limit once per kernel, device and
 // size (later launches of the same or a smaller size skip the call).
 cudaError_t ensure_smem(const void* kernel, size_t bytes);
@@ -48,6 +52,8 @@ struct DevBatch {
     int exchange_impl;              // 0 automatic, 1 global-memory clusters, 2 shared-memory staged
     int max_half;                   // largest L^3/2 of the batch
     int* err;                       // device error word (bit 0: a bounded wait gave up)
+    unsigned long long wait_limit;  // polls of a bounded mbarrier wait before it gives up
+    int wait_fault;                 // test hook: the bulk-copy half sweep leaves one stage un-issued
     const int4* tma_items;          // (sample, k0, first replica, count) of the bulk-copy half sweep
     int n_tma_items;
     int tma_smem;                   // dynamic shared memory of the bulk-copy half sweep

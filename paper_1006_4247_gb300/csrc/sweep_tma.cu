@@ -27,7 +27,6 @@ namespace ptk {
 constexpr int TMA_THREADS = 256;
 constexpr int TMA_V = 4;
 constexpr int TMA_STAGES = 4;  // replicas in flight per CTA (one CTA per SM)
-constexpr unsigned long long TMA_SPIN_LIMIT = 1ull << 22;
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
     return (unsigned)__cvta_generic_to_shared(p);
@@ -60,8 +59,9 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
 }
 
 // Bounded wait for the phase with the given parity; false if it gave up.
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity) {
-    for (unsigned long long it = 0; it < TMA_SPIN_LIMIT; ++it)
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity,
+                                                  unsigned long long limit) {
+    for (unsigned long long it = 0; it < limit; ++it)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
@@ -107,6 +107,7 @@ __global__ void __launch_bounds__(TMA_THREADS, 1) k_or_tma(DevBatch a, const int
     }
     __syncthreads();
     unsigned phase_bits = 0u;  // bit q: parity of the phase stage q waits for
+    unsigned inflight = 0u;    // thread 0: bit q set while stage q has copies not yet waited for
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
         const int4 it = items[item];  // (sample, k0, first replica, replica count)
         const SampleDesc& sd = a.samples[it.x];
@@ -151,8 +152,13 @@ __global__ void __launch_bounds__(TMA_THREADS, 1) k_or_tma(DevBatch a, const int
         // orders the CTA's earlier shared-memory reads before the copies)
         if (threadIdx.x == 0 && !s_abort) {
             fence_async_smem();
-            for (int q = 0; q < TMA_STAGES - 1 && q < it.w; ++q)
+            for (int q = 0; q < TMA_STAGES - 1 && q < it.w; ++q) {
+                // failure-path test hook: CTA 0 leaves its first stage
+                // un-issued, so the wait for it runs out
+                if (a.wait_fault && blockIdx.x == 0 && item == 0 && q == 0) continue;
                 tma_issue(a, sd, it.z + q, color, k0, P, plane, stage(q), stage(q) + 3 * Pp, &bar[q]);
+                inflight |= 1u << q;
+            }
         }
         __syncthreads();
         for (int i = 0; i < it.w; ++i) {
@@ -162,12 +168,15 @@ __global__ void __launch_bounds__(TMA_THREADS, 1) k_or_tma(DevBatch a, const int
                 const int sa = ahead % TMA_STAGES;
                 fence_async_smem();
                 tma_issue(a, sd, it.z + ahead, color, k0, P, plane, stage(sa), stage(sa) + 3 * Pp, &bar[sa]);
+                inflight |= 1u << sa;
             }
-            if (!mbar_wait_bounded(&bar[st], (phase_bits >> st) & 1u)) {
+            if (mbar_wait_bounded(&bar[st], (phase_bits >> st) & 1u, a.wait_limit)) {
+                phase_bits ^= 1u << st;
+                inflight &= ~(1u << st);
+            } else {
                 atomicOr(a.err, 1);
                 s_abort = 1;
             }
-            phase_bits ^= 1u << st;
             __syncthreads();
             if (s_abort) break;
             const int r = it.z + i;
@@ -249,9 +258,12 @@ __global__ void __launch_bounds__(TMA_THREADS, 1) k_or_tma(DevBatch a, const int
         __syncthreads();  // J region free for the next item
     }
     if (s_abort && threadIdx.x == 0) {
-        // give the copies still in flight a bounded chance to land before the
-        // CTA's shared memory is released
-        for (int st = 0; st < TMA_STAGES; ++st) mbar_wait_bounded(&bar[st], (phase_bits >> st) & 1u);
+        // give the copies this CTA still has in flight a bounded chance to
+        // land before its shared memory is released (at least the default
+        // limit, however short the data waits were set)
+        const unsigned long long drain = a.wait_limit > WAIT_LIMIT_DEFAULT ? a.wait_limit : WAIT_LIMIT_DEFAULT;
+        for (int st = 0; st < TMA_STAGES; ++st)
+            if ((inflight >> st) & 1u) mbar_wait_bounded(&bar[st], (phase_bits >> st) & 1u, drain);
     }
 }
 

@@ -36,7 +36,8 @@ ENTRY_POINTS = ["pt_options_default", "pt_create", "pt_create_batch", "pt_sweep"
                 "pt_cycles", "pt_autotune", "pt_exchange",
                 "pt_measure", "pt_measure_device", "pt_get_stats", "pt_get_spins", "pt_set_spins",
                 "pt_set_params", "pt_set_rng_step", "pt_get_rng_step", "pt_save", "pt_load",
-                "pt_profile", "pt_profile_read", "pt_set_policy", "pt_energy_noalloc", "pt_destroy",
+                "pt_profile", "pt_profile_read", "pt_set_policy", "pt_set_wait_limit", "pt_energy_noalloc",
+                "pt_destroy",
                 "pt_last_error", "pt_mlp_create", "pt_mlp_num_params", "pt_mlp_set_params",
                 "pt_mlp_get_params", "pt_mlp_forward", "pt_mlp_loss_grad", "pt_mlp_train", "pt_mlp_ladder",
                 "pt_mlp_destroy"]
@@ -88,6 +89,7 @@ def load_library(path: str = LIB_PATH):
                 "pt_profile": (ip, [vp, ip]),
                 "pt_profile_read": (ip, [vp, dp, i64p]),
                 "pt_set_policy": (ip, [vp, ip]),
+                "pt_set_wait_limit": (ip, [vp, C.c_ulonglong, ip]),
                 "pt_energy_noalloc": (ip, [vp, ip, ip, ip, vp, vp, vp]),
                 "pt_get_stats": (ip, [vp, i64p, i64p, i64p, i32p]),
                 "pt_get_spins": (ip, [vp, ip, ip, ip, dp]),
@@ -219,6 +221,10 @@ def pt_profile_read(h):
 def pt_set_policy(h, policy):
     policy = POLICIES.get(policy, policy) if isinstance(policy, str) else int(policy)
     _check(load_library().pt_set_policy(h, policy))
+
+
+def pt_set_wait_limit(h, limit=0, inject=False):
+    _check(load_library().pt_set_wait_limit(h, int(limit), 1 if inject else 0))
 
 
 def pt_energy_noalloc(d_spins, precision, L, n_configs, d_couplings, d_energy, stream=None):
@@ -386,6 +392,11 @@ class Engine:
 
     def set_policy(self, policy):
         pt_set_policy(self.h, policy)
+
+    def set_wait_limit(self, limit=0, inject=False):
+        """Poll limit of the bounded device-side waits (0: default) and the
+        hook that makes one of them run out (see pt_set_wait_limit)."""
+        pt_set_wait_limit(self.h, limit, inject)
 
     def measure_device(self, d_energy=None, d_overlap=None, d_chi=None):
         """Enqueue the reductions; results also go to the given device

@@ -135,3 +135,40 @@ def test_measure_device_and_profiler():
     assert n["exchange"] == 1 and n["measure"] == 1 and sum(n.values()) >= 4
     assert all(v >= 0 for v in ms.values())
     eng.close()
+
+
+def test_bounded_wait_gives_up_and_handle_stays_usable(monkeypatch):
+    """The bulk-copy half sweep's mbarrier wait runs out (one stage's copies
+    are never issued): the next synchronising call returns PT_ERR_TIMEOUT once,
+    the spins stay unit vectors, and the same handle then sweeps exactly like
+    a handle that never failed."""
+    from gpu_util import set_random_state
+    L, S, NT, C = 16, 1, 3, 2
+    monkeypatch.setenv("PT_TMA", "1")
+    eng, J, B = make_engine(L, S, NT, C, "fp32", seed=9)
+    eng.set_policy("streaming")
+    monkeypatch.delenv("PT_TMA")
+    ref, _, _ = make_engine(L, S, NT, C, "fp32", seed=9)
+    ref.set_policy("streaming")
+    eng.set_wait_limit(1024, inject=True)
+    eng.sweep(0, 1)  # colour 0 through the bulk-copy kernel, colour 1 with the energy
+    with pytest.raises(pt.PtError) as ei:
+        eng.energies()
+    assert ei.value.status == pt.PT_ERR_TIMEOUT
+    s = get_state(eng, S, C, NT)
+    assert np.abs(np.linalg.norm(s, axis=-1) - 1.0).max() < 1e-5
+    eng.set_wait_limit(0, inject=False)
+    out = []
+    for e in (eng, ref):
+        set_random_state(e, S, C, NT, L, seed=19)
+        e.sweep(0, 3)
+        out.append((get_state(e, S, C, NT), e.energies()))
+    assert np.abs(out[0][0] - out[1][0]).max() <= 1e-6
+    assert np.abs(out[0][1] - out[1][1]).max() <= 1e-3
+    eng.close()
+    ref.close()
+    plain, _, _ = make_engine(8, 1, 3, 2, "fp32")
+    with pytest.raises(pt.PtError) as ei:
+        plain.set_wait_limit(16, inject=True)  # no bulk-copy kernel to fault
+    assert ei.value.status == pt.PT_ERR_STATE
+    plain.close()
