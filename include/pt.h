@@ -289,15 +289,25 @@ pt_status pt_cycles(pt_handle h, int n_cycles, int n_hb, int n_or, const int *n_
                     pt_mode mode, int measure);
 
 /* Autotuner: for every lattice size of the batch, time each candidate way of
- * running the sweeps (shared-memory resident blocks or streaming half sweeps,
- * with 4, 2 or 1 sites per thread where the row length allows) on the batch
- * itself, a warm-up and two blocks of n_hb + n_or sweeps each, and keep the
- * fastest under PT_POLICY_AUTO.  The chain state (spins, energies, step
- * counter) is restored, so tuning does not change the chain.  Optional host
- * outputs per sample: choice[s] = vector width (+10 when resident),
- * best_ms[s] = time of one block with the chosen path.  Allocates a temporary
- * copy of the spins on the device. */
+ * running the sweeps (shared-memory resident blocks -- one CTA, a cluster of
+ * 1024-thread CTAs, or a "narrow" cluster of 512-thread CTAs, two per SM --
+ * or streaming half sweeps, with 4, 2 or 1 sites per thread where the row
+ * length allows) on the batch itself, a warm-up and two blocks of
+ * n_hb + n_or sweeps each, and keep the fastest under PT_POLICY_AUTO.  The
+ * chain state (spins, energies, step counter) is restored, so tuning does not
+ * change the chain.  Optional host outputs per sample: choice[s] in the
+ * encoding of pt_get_paths, best_ms[s] = time of one block with the chosen
+ * path.  Allocates a temporary copy of the spins on the device. */
 pt_status pt_autotune(pt_handle h, int n_hb, int n_or, int *choice, double *best_ms);
+
+/* The sweep path of every sample now (host int [n_samples]): the vector
+ * width (sites per thread: 4, 2 or 1) for streaming half sweeps, + 10 for the
+ * resident kernels with one CTA or a cluster of 1024-thread CTAs, + 20 for a
+ * narrow cluster of 512-thread CTAs; ctas[s] (host int [n_samples] or NULL)
+ * = CTAs per replica (0 when streaming).  PT_CL_NARROW=1 in the environment
+ * when the handle is created selects narrow clusters wherever they exist,
+ * until pt_autotune decides. */
+pt_status pt_get_paths(pt_handle h, int *choice, int *ctas);
 
 /* Release all device memory of the handle.  NULL is accepted. */
 pt_status pt_destroy(pt_handle h);

@@ -108,7 +108,8 @@ struct pt_engine {
     std::vector<int> stile_idx;       // streaming subset of `tiles`
     std::vector<int> res_reps;        // replicas of resident samples
     std::vector<int> tuned_vec;       // per sample: vector width chosen by pt_autotune (0: default)
-    std::vector<int> tuned_res;       // per sample: -1 default, 0 streaming, 1 resident (pt_autotune)
+    std::vector<int> tuned_res;       // per sample: -1 default, 0 streaming, 1 resident, 2 narrow clusters (pt_autotune)
+    bool narrow_default = false;      // PT_CL_NARROW=1 at creation: narrow clusters unless tuned otherwise
     size_t tile_cap = 0;              // capacity of the tile and partial arrays
     int* d_stiles = nullptr;
     int* d_res_reps = nullptr;
@@ -288,9 +289,18 @@ void choose_paths(pt_engine* e) {
         bool res;
         if (e->policy == PT_POLICY_STREAMING) res = false;
         else if (e->policy == PT_POLICY_RESIDENT) res = fits;
-        else res = (!e->tuned_res.empty() && e->tuned_res[s] >= 0) ? (e->tuned_res[s] == 1 && fits) : fits;
+        else res = (!e->tuned_res.empty() && e->tuned_res[s] >= 0) ? (e->tuned_res[s] >= 1 && fits) : fits;
         sd.vec = res ? (resident_cluster(sd, e->fp64, vec) > 0 ? vec : def_vec) : vec;
         sd.resident = res ? resident_cluster(sd, e->fp64, sd.vec) : 0;  // CTAs per replica
+        sd.narrow = 0;
+        const bool tuned = !e->tuned_res.empty() && e->tuned_res[s] >= 0;
+        if (res && (tuned ? e->tuned_res[s] == 2 : e->narrow_default)) {
+            const int cn = resident_cluster_narrow(sd, e->fp64, sd.vec);
+            if (cn > 0) {
+                sd.resident = cn;
+                sd.narrow = 1;
+            }
+        }
         sd.tiles_per_rep = (sd.half + TILE * sd.vec - 1) / (TILE * sd.vec);
     }
 }
@@ -332,12 +342,13 @@ pt_status rebuild_lists(pt_engine* e) {
     e->any_streaming = false;
     for (const SampleDesc& sd : e->samples)
         if (!sd.resident) e->any_streaming = true;
-    // resident replicas grouped by CTAs per replica (1, 2, 4, 8)
-    for (int g = 0; g < 4; ++g) {
+    // resident replicas grouped by path (one CTA; wide or narrow clusters of
+    // 2, 4, 8 CTAs)
+    for (int g = 0; g < RES_GROUPS; ++g) {
         d.rcl_begin[g] = (int)e->res_reps.size();
         d.rcl_half[g] = 0;
         for (const SampleDesc& sd : e->samples) {
-            if (sd.resident != (1 << g)) continue;
+            if (!sd.resident || resident_group(sd.resident, sd.narrow != 0) != g) continue;
             for (int q = 0; q < e->C * sd.NT; ++q) e->res_reps.push_back(sd.r0 + q);
             d.rcl_half[g] = std::max(d.rcl_half[g], sd.half);
         }
@@ -493,6 +504,12 @@ pt_status create_impl(pt_handle* out, int n_samples, const int* Ls, const int* N
         }
     }
     for (const SampleDesc& sd : e->samples) e->max_half = std::max(e->max_half, sd.half);
+    {
+        // PT_CL_NARROW=1 prefers clusters of 512-thread CTAs (two per SM) for
+        // samples too large for one CTA, until pt_autotune decides
+        const char* ev = std::getenv("PT_CL_NARROW");
+        e->narrow_default = ev && std::strcmp(ev, "1") == 0;
+    }
     choose_paths(e);
     e->R = r;
     e->T = 0;
@@ -922,14 +939,16 @@ pt_status pt_autotune(pt_handle e, int n_hb, int n_or, int* choice, double* best
     for (int L : Ls) {
         const int hL = L / 2;
         std::vector<std::pair<int, int>> cand;  // (resident, vec)
-        for (int res = 1; res >= 0; --res)
+        for (int res = 2; res >= 0; --res)
             for (int vec : {4, 2, 1}) {
                 if (e->fp64 && vec == 4) continue;
                 if (hL % vec) continue;
                 if (res) {
                     bool ok = true;
                     for (const SampleDesc& sd : e->samples)
-                        if (sd.L == L && resident_cluster(sd, e->fp64, vec) == 0) ok = false;
+                        if (sd.L == L && (res == 2 ? resident_cluster_narrow(sd, e->fp64, vec)
+                                                   : resident_cluster(sd, e->fp64, vec)) == 0)
+                            ok = false;
                     if (!ok) continue;
                 }
                 cand.push_back({res, vec});
@@ -983,7 +1002,8 @@ pt_status pt_autotune(pt_handle e, int n_hb, int n_or, int* choice, double* best
     if (saved_policy != PT_POLICY_AUTO) e->policy = PT_POLICY_AUTO;
     if (st != PT_OK) return st;
     for (int s = 0; s < e->S; ++s) {
-        if (choice) choice[s] = e->samples[s].resident ? 10 + e->samples[s].vec : e->samples[s].vec;
+        const SampleDesc& sd = e->samples[s];
+        if (choice) choice[s] = sd.resident ? (sd.narrow ? 20 : 10) + sd.vec : sd.vec;
         if (best_ms) best_ms[s] = best[s];
     }
     return sync(e);
@@ -1259,6 +1279,16 @@ pt_status pt_set_wait_limit(pt_handle e, unsigned long long limit, int inject) {
     if (st != PT_OK) return st;
     e->d.wait_limit = limit ? limit : WAIT_LIMIT_DEFAULT;
     e->d.wait_fault = inject ? 1 : 0;
+    return PT_OK;
+}
+
+pt_status pt_get_paths(pt_handle e, int* choice, int* ctas) {
+    if (!e || !choice) return fail(PT_ERR_ARG, "NULL argument");
+    for (int s = 0; s < e->S; ++s) {
+        const SampleDesc& sd = e->samples[s];
+        choice[s] = sd.resident ? (sd.narrow ? 20 : 10) + sd.vec : sd.vec;
+        if (ctas) ctas[s] = sd.resident;
+    }
     return PT_OK;
 }
 

@@ -164,21 +164,24 @@ __device__ __forceinline__ T decim_D(T n, T b1, T b2, T db, T lr) {
 // ---------------------------------------------------------------------------
 template <typename T, int V>
 __device__ __forceinline__ void decimation_chain(const DevBatch& a, cg::cluster_group& cl, ChainSmem& sm,
-                                                 const ChainDesc& cd, const SampleDesc& sd, int ch, int cs, int rank);
+                                                 const DecimPairs<T, MAX_NT>& dp, const ChainDesc& cd,
+                                                 const SampleDesc& sd, int ch, int cs, int rank);
 
 template <typename T>
 __global__ void __launch_bounds__(EX_THREADS, 2) k_exchange_decimation(DevBatch a) {
     __shared__ ChainSmem sm;
+    __shared__ DecimPairs<T, MAX_NT> dp;
     cg::cluster_group cl = cg::this_cluster();
     const int cs = (int)cl.num_blocks(), rank = (int)cl.block_rank();
     const int ch = blockIdx.x / cs;
     const ChainDesc cd = a.chains[ch];
     const SampleDesc& sd = a.samples[cd.s];
     const int NT = sd.NT, half = sd.half;
+    dp.load(a.betas + sd.beta_off, NT);  // visible after load_chain's barrier
     load_chain(a, cd, NT, sm, ch);
-    if (sd.vec == 4) decimation_chain<T, (sizeof(T) == 4 ? 4 : 2)>(a, cl, sm, cd, sd, ch, cs, rank);
-    else if (sd.vec == 2) decimation_chain<T, 2>(a, cl, sm, cd, sd, ch, cs, rank);
-    else decimation_chain<T, 1>(a, cl, sm, cd, sd, ch, cs, rank);
+    if (sd.vec == 4) decimation_chain<T, (sizeof(T) == 4 ? 4 : 2)>(a, cl, sm, dp, cd, sd, ch, cs, rank);
+    else if (sd.vec == 2) decimation_chain<T, 2>(a, cl, sm, dp, cd, sd, ch, cs, rank);
+    else decimation_chain<T, 1>(a, cl, sm, dp, cd, sd, ch, cs, rank);
     if (rank == 0) store_chain(a, cd, NT, sm, ch);
     cl.sync();  // no CTA leaves while others may still read its shared memory
 }
@@ -187,8 +190,8 @@ __global__ void __launch_bounds__(EX_THREADS, 2) k_exchange_decimation(DevBatch 
 // vectors of the decimated colour (16-byte loads of the neighbour rows).
 template <typename T, int V>
 __device__ __forceinline__ void decimation_chain(const DevBatch& a, cg::cluster_group& cl, ChainSmem& sm,
-                                                 const ChainDesc& cd, const SampleDesc& sd, int ch, int cs,
-                                                 int rank) {
+                                                 const DecimPairs<T, MAX_NT>& dp, const ChainDesc& cd,
+                                                 const SampleDesc& sd, int ch, int cs, int rank) {
     const int NT = sd.NT, half = sd.half;
     int lo, hi;
     slice(half / V, rank, cs, lo, hi);  // in vectors
@@ -196,20 +199,17 @@ __device__ __forceinline__ void decimation_chain(const DevBatch& a, cg::cluster_
     hi *= V;
     int pub = 0;
     const unsigned long long step = *a.d_step;
-    const double* beta = a.betas + sd.beta_off;
     T* pool = (T*)a.spins + a.chain_off[ch];
     const uint4 wd = rng_words(a.seed, (uint32_t)cd.s, 0u, (uint32_t)cd.copy, step, 3u);
     const int d0 = (int)(wd.x & 1u);
     for (int i = 0; i + 1 < NT; ++i) {
         const int d = (d0 + i) & 1;
-        const double b1 = beta[i], b2 = beta[i + 1];
-        const T b1t = (T)b1, b2t = (T)b2;
+        const T b1t = dp.b[i], b2t = dp.b[i + 1];
         const T* c1 = pool + (long long)sm.buf[i] * (6LL * half);
         const T* c2 = pool + (long long)sm.buf[i + 1] * (6LL * half);
         const float* Jd = a.J + sd.J_off + d * 3 * half;
         const float* Jk = a.J + sd.J_off + (1 - d) * 3 * half;
-        const T dbt = (T)(b2 - b1);
-        const T lr = b1 > 0.0 ? (T)log(b2 / b1) : (T)0;
+        const T dbt = dp.db[i], lr = dp.lr[i];
         T part[1] = {(T)0};
         for (int h0 = lo + (int)threadIdx.x * V; h0 < hi; h0 += (int)blockDim.x * V) {
             const VRow q = vrow<V>(sd, d, h0);

@@ -250,16 +250,17 @@ template <typename T>
 __global__ void __launch_bounds__(SX_THREADS, 1) k_exchange_decimation_smem(DevBatch a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ SxSmem sm;
+    __shared__ DecimPairs<T, SX_MAX_NT> dp;
     const int ch = blockIdx.x;
     const ChainDesc cd = a.chains[ch];
     const SampleDesc& sd = a.samples[cd.s];
     const int NT = sd.NT, half = sd.half, n3 = 6 * half;
     T* const slots = reinterpret_cast<T*>(smem_raw);
     auto slot = [&](int q) { return slots + (size_t)q * n3; };
+    dp.load(a.betas + sd.beta_off, NT);  // visible after sx_load_state's barrier
     sx_load_state(a, cd, NT, sm);
     T* pool = (T*)a.spins + a.chain_off[ch];
     const unsigned long long step = *a.d_step;
-    const double* beta = a.betas + sd.beta_off;
     const uint4 wd = rng_words(a.seed, (uint32_t)cd.s, 0u, (uint32_t)cd.copy, step, 3u);
     const int d0 = (int)(wd.x & 1u);
     int A = 0;
@@ -272,9 +273,7 @@ __global__ void __launch_bounds__(SX_THREADS, 1) k_exchange_decimation_smem(DevB
         sx_copy(slot(B), pool + (long long)ownerB * n3, n3);
         __syncthreads();
         const int d = (d0 + i) & 1;
-        const double b1 = beta[i], b2 = beta[i + 1];
-        const T b1t = (T)b1, b2t = (T)b2, dbt = (T)(b2 - b1);
-        const T lr = b1 > 0.0 ? (T)log(b2 / b1) : (T)0;
+        const T b1t = dp.b[i], b2t = dp.b[i + 1], dbt = dp.db[i], lr = dp.lr[i];
         const float* Jd = a.J + sd.J_off + d * 3 * half;
         const float* Jk = a.J + sd.J_off + (1 - d) * 3 * half;
         T* c1 = slot(A);

@@ -7,6 +7,9 @@
 
 namespace ptk {
 
+// Groups of resident replicas (see DevBatch::rcl_begin).
+constexpr int RES_GROUPS = 7;
+
 // Polls of a bounded mbarrier wait before it gives up (the default of
 // DevBatch::wait_limit, and the least the drain after a failed wait uses).
 constexpr unsigned long long WAIT_LIMIT_DEFAULT = 1ull << 22;
@@ -61,9 +64,11 @@ struct DevBatch {
     // streaming subset is grouped the same way inside stiles
     int vclass_begin[3], vclass_count[3], vclass_width[3];
     int sclass_begin[3], sclass_count[3];
-    // resident replicas grouped by CTAs per replica (1, 2, 4, 8): slices of
-    // res_reps and the largest L^3/2 of each group
-    int rcl_begin[4], rcl_count[4], rcl_half[4];
+    // resident replicas grouped by path: 0 one CTA per replica; 1, 2, 3
+    // clusters of 2, 4, 8 CTAs of 1024 threads; 4, 5, 6 clusters of 2, 4, 8
+    // CTAs of 512 threads (two per SM): slices of res_reps and the largest
+    // L^3/2 of each group
+    int rcl_begin[RES_GROUPS], rcl_count[RES_GROUPS], rcl_half[RES_GROUPS];
     // cooling/heating with the pair staged in shared memory: the heated
     // configuration of every pair (pair index x 6 max_half elements), its
     // energy and ln det J_C, computed before the pairs are walked (NULL when
@@ -117,6 +122,14 @@ bool resident_supported(const SampleDesc& sd, bool fp64, int vec);
 // (resident_supported), else the smallest cluster of 2, 4 or 8 CTAs that can
 // (each CTA a slab of L/size z planes), 0 when none can.
 int resident_cluster(const SampleDesc& sd, bool fp64, int vec);
+
+// Narrow clusters: the smallest cluster of 2, 4 or 8 CTAs of 512 threads whose
+// slab fits two CTAs per SM (<= 110 KB), for samples that do not fit one CTA;
+// 0 if none.
+int resident_cluster_narrow(const SampleDesc& sd, bool fp64, int vec);
+
+// Group of a resident replica (DevBatch::rcl_begin) for cs CTAs per replica.
+int resident_group(int cs, bool narrow);
 // Kernels one resident block launches (one per non-empty group).
 int resident_launch_count(const DevBatch& b);
 cudaError_t launch_resident(const DevBatch& b, bool fp64, int n_hb, int n_or, cudaStream_t st);

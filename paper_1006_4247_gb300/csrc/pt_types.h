@@ -39,8 +39,8 @@ struct SampleDesc {
     int tiles_per_rep;        // ceil(half / (TILE * vec))
     int vec;                  // sites per thread in the half sweep (4, 2 or 1)
     int tma_planes;           // z planes per item of the bulk-copy half sweep (0: not used)
-    int resident;             // 1: this sample's sweeps run in the shared-memory resident kernel
-    int pad;
+    int resident;             // CTAs per replica of the shared-memory resident sweeps (0: streaming)
+    int narrow;               // 1: clusters of 512-thread CTAs, two per SM (resident > 1 only)
 };
 
 struct ChainDesc {

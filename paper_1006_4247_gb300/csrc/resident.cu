@@ -255,7 +255,8 @@ __global__ void __launch_bounds__(RES_THREADS, 2) k_resident(DevBatch a, int n_h
 // separates the half sweeps.  Every CTA executes the same sequence of
 // barriers, so no CTA waits on a condition only another one can change.
 // ---------------------------------------------------------------------------
-constexpr int CL_THREADS = 1024;
+constexpr int CL_THREADS = 1024;      // wide clusters: one CTA per SM
+constexpr int CL_THREADS_NARROW = 512; // narrow clusters: two CTAs per SM (slab <= 110 KB)
 
 // Neighbour field of V sites of a slab row; the z+ row may live in the next
 // CTA (othP) and the z- row with its couplings in the previous one (othM,
@@ -308,7 +309,7 @@ struct Slab {
     int hl, Lz, k0, rank, cs;  // sites per colour, planes, first plane, CTA rank, cluster size
 };
 
-template <typename T, int V, int KIND, bool ENERGY>
+template <typename T, int NTH, int V, int KIND, bool ENERGY>
 __device__ __forceinline__ T cl_halfsweep(cg::cluster_group& cl, T* __restrict__ sm, const float* __restrict__ J,
                                           const SampleDesc& sd, const Slab& sb, int color, T beta,
                                           unsigned long long seed, uint32_t sample, uint32_t rep_id,
@@ -319,7 +320,7 @@ __device__ __forceinline__ T cl_halfsweep(cg::cluster_group& cl, T* __restrict__
     const float* Jown = J + color * 3 * hl;
     const float* Joth = J + (1 - color) * 3 * hl;
     T e = (T)0;
-    for (int h0 = (int)threadIdx.x * V; h0 < hl; h0 += CL_THREADS * V) {
+    for (int h0 = (int)threadIdx.x * V; h0 < hl; h0 += NTH * V) {
         const int row = (int)fdiv((uint32_t)h0, sd.div_hL);  // slab row j + L kl
         const int ih0 = h0 - row * hL;
         const int kl = (int)fdiv((uint32_t)row, sd.div_L);
@@ -444,7 +445,7 @@ __device__ __forceinline__ T cl_or_one(cg::cluster_group& cl, T* __restrict__ sm
     return e;
 }
 
-template <typename T, int V>
+template <typename T, int NTH, int V>
 __device__ __forceinline__ T cl_block(cg::cluster_group& cl, T* sm, const float* J, const DevBatch& a,
                                       const SampleDesc& sd, const Slab& sb, const int4& rd, int n_hb, int n_or) {
     const T beta = (T)a.betas[sd.beta_off + rd.z];
@@ -456,14 +457,14 @@ __device__ __forceinline__ T cl_block(cg::cluster_group& cl, T* sm, const float*
         for (int c = 0; c < 2; ++c, ++kstep) {
             const unsigned long long st = step0 + (unsigned long long)kstep;
             if (kstep == total - 1)
-                e = cl_halfsweep<T, 1, 1, true>(cl, sm, J, sd, sb, c, beta, a.seed, (uint32_t)rd.x, (uint32_t)rd.w,
+                e = cl_halfsweep<T, NTH, 1, 1, true>(cl, sm, J, sd, sb, c, beta, a.seed, (uint32_t)rd.x, (uint32_t)rd.w,
                                                 st);
             else
-                cl_halfsweep<T, 1, 1, false>(cl, sm, J, sd, sb, c, beta, a.seed, (uint32_t)rd.x, (uint32_t)rd.w,
+                cl_halfsweep<T, NTH, 1, 1, false>(cl, sm, J, sd, sb, c, beta, a.seed, (uint32_t)rd.x, (uint32_t)rd.w,
                                              st);
             cl.sync();
         }
-    if (sb.hl <= CL_THREADS * V) {
+    if (sb.hl <= NTH * V) {
         const bool xsh = (32 % (sd.hL / V) == 0) && ((sb.hl / V) % 32 == 0);
         const VecIdxCl q = vec_idx_cl<V>(sd, sb, (int)threadIdx.x * V, xsh);
         for (int o = 0; o < n_or; ++o)
@@ -482,19 +483,21 @@ __device__ __forceinline__ T cl_block(cg::cluster_group& cl, T* sm, const float*
     for (int o = 0; o < n_or; ++o)
         for (int c = 0; c < 2; ++c, ++kstep) {
             if (kstep == total - 1)
-                e = cl_halfsweep<T, V, 0, true>(cl, sm, J, sd, sb, c, beta, a.seed, (uint32_t)rd.x, (uint32_t)rd.w,
+                e = cl_halfsweep<T, NTH, V, 0, true>(cl, sm, J, sd, sb, c, beta, a.seed, (uint32_t)rd.x, (uint32_t)rd.w,
                                                 0ull);
             else
-                cl_halfsweep<T, V, 0, false>(cl, sm, J, sd, sb, c, beta, a.seed, (uint32_t)rd.x, (uint32_t)rd.w,
+                cl_halfsweep<T, NTH, V, 0, false>(cl, sm, J, sd, sb, c, beta, a.seed, (uint32_t)rd.x, (uint32_t)rd.w,
                                              0ull);
             cl.sync();
         }
     return e;
 }
 
-// One cluster per replica of the group that starts at res_reps[begin].
-template <typename T>
-__global__ void __launch_bounds__(CL_THREADS, 1) k_resident_cl(DevBatch a, int n_hb, int n_or, int begin) {
+// One cluster per replica of the group that starts at res_reps[begin]; NTH
+// threads per CTA (1024: one CTA per SM; 512: two CTAs of different
+// clusters share an SM, so one's barrier waits overlap the other's work).
+template <typename T, int NTH>
+__global__ void __launch_bounds__(NTH, 1024 / NTH) k_resident_cl(DevBatch a, int n_hb, int n_or, int begin) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[32];
     __shared__ double cta_total;
@@ -518,13 +521,13 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_resident_cl(DevBatch a, int n
     const T* g = (const T*)a.spins + a.chain_off[rd.y] + (long long)a.bufmap[r] * (6LL * half);
     const float* gJ = a.J + sd.J_off;
     constexpr int VW = 16 / sizeof(T);
-    for (int q = threadIdx.x * VW; q < n3; q += CL_THREADS * VW) {
+    for (int q = threadIdx.x * VW; q < n3; q += NTH * VW) {
         const int run = q / hl, off = q - run * hl;  // hl is a multiple of VW
         T v[VW];
         ldv<T, VW>(g + (long long)run * half + rank * hl + off, v);
         stv<T, VW>(sm + q, v);
     }
-    for (int q = threadIdx.x * 4; q < n3; q += CL_THREADS * 4) {
+    for (int q = threadIdx.x * 4; q < n3; q += NTH * 4) {
         const int run = q / hl, off = q - run * hl;
         float v[4];
         ldv_nc<float, 4>(gJ + (long long)run * half + rank * hl + off, v);
@@ -532,11 +535,12 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_resident_cl(DevBatch a, int n
     }
     cl.sync();  // every slab loaded before any neighbour reads it
     T e[1];
-    if (sizeof(T) == 4 && sd.vec == 4) e[0] = cl_block<T, (sizeof(T) == 4 ? 4 : 2)>(cl, sm, sJ, a, sd, sb, rd, n_hb, nor);
-    else e[0] = cl_block<T, 2>(cl, sm, sJ, a, sd, sb, rd, n_hb, nor);
+    if (sizeof(T) == 4 && sd.vec == 4)
+        e[0] = cl_block<T, NTH, (sizeof(T) == 4 ? 4 : 2)>(cl, sm, sJ, a, sd, sb, rd, n_hb, nor);
+    else e[0] = cl_block<T, NTH, 2>(cl, sm, sJ, a, sd, sb, rd, n_hb, nor);
     // the last barrier of the block has passed: the slab is final
     T* gw = (T*)a.spins + a.chain_off[rd.y] + (long long)a.bufmap[r] * (6LL * half);
-    for (int q = threadIdx.x * VW; q < n3; q += CL_THREADS * VW) {
+    for (int q = threadIdx.x * VW; q < n3; q += NTH * VW) {
         const int run = q / hl, off = q - run * hl;
         T v[VW];
         ldv<T, VW>(sm + q, v);
@@ -582,21 +586,40 @@ int resident_cluster(const SampleDesc& sd, bool fp64, int vec) {
     return 0;
 }
 
+int resident_cluster_narrow(const SampleDesc& sd, bool fp64, int vec) {
+    if (resident_supported(sd, fp64, vec)) return 0;  // one CTA per replica already fits
+    if (vec != 4 && vec != 2) return 0;
+    if (fp64 && vec != 2) return 0;
+    if (sd.hL % vec) return 0;
+    for (int cs : {2, 4, 8}) {
+        if (sd.L % cs) continue;
+        const int hl = sd.half / cs;
+        if (hl % 4 != 0) continue;
+        if (resident_smem_bytes(hl, fp64) <= 110 * 1024) return cs;  // two CTAs per SM
+    }
+    return 0;
+}
+
+int resident_group(int cs, bool narrow) {
+    const int lg = cs == 1 ? 0 : cs == 2 ? 1 : cs == 4 ? 2 : 3;
+    return lg == 0 ? 0 : lg + (narrow ? 3 : 0);
+}
+
 int resident_launch_count(const DevBatch& b) {
     int n = 0;
-    for (int g = 0; g < 4; ++g) n += b.rcl_count[g] > 0;
+    for (int g = 0; g < RES_GROUPS; ++g) n += b.rcl_count[g] > 0;
     return n;
 }
 
-template <typename T>
+template <typename T, int NTH>
 static cudaError_t launch_cl(const DevBatch& b, int g, int n_hb, int n_or, cudaStream_t st) {
-    const int cs = 1 << g;
+    const int cs = 1 << ((g - 1) % 3 + 1);
     const size_t smem = resident_smem_bytes(b.rcl_half[g] / cs, sizeof(T) == 8);
-    cudaError_t e = ensure_smem((const void*)k_resident_cl<T>, smem);
+    cudaError_t e = ensure_smem((const void*)k_resident_cl<T, NTH>, smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(b.rcl_count[g] * cs), 1, 1);
-    cfg.blockDim = dim3(CL_THREADS, 1, 1);
+    cfg.blockDim = dim3(NTH, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
@@ -606,7 +629,7 @@ static cudaError_t launch_cl(const DevBatch& b, int g, int n_hb, int n_or, cudaS
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_resident_cl<T>, b, n_hb, n_or, b.rcl_begin[g]);
+    return cudaLaunchKernelEx(&cfg, k_resident_cl<T, NTH>, b, n_hb, n_or, b.rcl_begin[g]);
 }
 
 cudaError_t launch_resident(const DevBatch& b, bool fp64, int n_hb, int n_or, cudaStream_t st) {
@@ -625,9 +648,14 @@ cudaError_t launch_resident(const DevBatch& b, bool fp64, int n_hb, int n_or, cu
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    for (int g = 1; g < 4; ++g) {
+    for (int g = 1; g < RES_GROUPS; ++g) {
         if (b.rcl_count[g] == 0) continue;
-        e = fp64 ? launch_cl<double>(b, g, n_hb, n_or, st) : launch_cl<float>(b, g, n_hb, n_or, st);
+        if (g <= 3)
+            e = fp64 ? launch_cl<double, CL_THREADS>(b, g, n_hb, n_or, st)
+                     : launch_cl<float, CL_THREADS>(b, g, n_hb, n_or, st);
+        else
+            e = fp64 ? launch_cl<double, CL_THREADS_NARROW>(b, g, n_hb, n_or, st)
+                     : launch_cl<float, CL_THREADS_NARROW>(b, g, n_hb, n_or, st);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

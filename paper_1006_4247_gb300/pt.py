@@ -33,7 +33,7 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 # Entry points declared in include/pt.h (the symbol test checks this list
 # against the header).
 ENTRY_POINTS = ["pt_options_default", "pt_create", "pt_create_batch", "pt_sweep", "pt_sweep_samples",
-                "pt_cycles", "pt_autotune", "pt_exchange",
+                "pt_cycles", "pt_autotune", "pt_get_paths", "pt_exchange",
                 "pt_measure", "pt_measure_device", "pt_get_stats", "pt_get_spins", "pt_set_spins",
                 "pt_set_params", "pt_set_rng_step", "pt_get_rng_step", "pt_save", "pt_load",
                 "pt_profile", "pt_profile_read", "pt_set_policy", "pt_set_wait_limit", "pt_energy_noalloc",
@@ -83,6 +83,7 @@ def load_library(path: str = LIB_PATH):
                 "pt_sweep_samples": (ip, [vp, ip, C.POINTER(C.c_int)]),
                 "pt_cycles": (ip, [vp, ip, ip, ip, C.POINTER(C.c_int), ip, ip]),
                 "pt_autotune": (ip, [vp, ip, ip, C.POINTER(C.c_int), dp]),
+                "pt_get_paths": (ip, [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
                 "pt_exchange": (ip, [vp, ip, fp]),
                 "pt_measure": (ip, [vp, dp, dp, dp]),
                 "pt_measure_device": (ip, [vp, vp, vp, vp]),
@@ -364,6 +365,13 @@ class Engine:
 
     def cycles(self, n_cycles, n_hb=1, n_or=1, mode="plain", measure=False, n_or_samples=None):
         pt_cycles(self.h, n_cycles, n_hb, n_or, mode, measure, n_or_samples)
+
+    def paths(self):
+        """Per-sample sweep path codes (see pt_get_paths) and CTAs per replica."""
+        ch = (C.c_int * self.S)()
+        ct = (C.c_int * self.S)()
+        _check(load_library().pt_get_paths(self.h, ch, ct))
+        return np.array(ch[:], np.int32), np.array(ct[:], np.int32)
 
     def autotune(self, n_hb=1, n_or=1):
         return pt_autotune(self.h, n_hb, n_or, self.S)

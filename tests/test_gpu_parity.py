@@ -302,6 +302,45 @@ def test_resident_and_streaming_paths_fp32(L):
     assert np.abs(res["resident"][1] - res["streaming"][1]).max() <= 1e-3
 
 
+@pytest.mark.parametrize("L,precision,cs", [(24, "fp32", 4), (32, "fp32", 8), (24, "fp64", 8)])
+def test_narrow_cluster_path_vs_oracle(L, precision, cs):
+    """Clusters of 512-thread CTAs (two per SM; L = 24 in slabs of 6 planes
+    and L = 32 of 4 in float, L = 24 of 3 in double): one heat-bath and two
+    overrelaxation sweeps against the streaming half sweeps and, in double,
+    against the oracle site by site."""
+    S, C, NT, seed = 2, 2, 2, 65
+    eng, J, B = _engine_env({"PT_CL_NARROW": "1"}, L, S, NT, C, precision, seed=seed)
+    choice, ctas = eng.paths()
+    assert (choice // 10 == 2).all() and (ctas == cs).all()
+    st = set_random_state(eng, S, C, NT, L, seed=9)
+    step0 = 777
+    eng.step = step0
+    eng.sweep(1, 2)
+    out = get_state(eng, S, C, NT)
+    H = eng.energies()
+    ref_eng, _, _ = make_engine(L, S, NT, C, precision, seed=seed)
+    ref_eng.set_policy("streaming")
+    for s in range(S):
+        for c in range(C):
+            for b in range(NT):
+                ref_eng.set_spins(s, c, b, st[s, c, b])
+    ref_eng.step = step0
+    ref_eng.sweep(1, 2)
+    assert np.abs(get_state(ref_eng, S, C, NT) - out).max() <= (1e-14 if precision == "fp64" else 1e-6)
+    ref_eng.close()
+    if precision == "fp64":  # float: the streaming path above is itself checked against the oracle
+        for s in range(S):
+            for c in range(C):
+                for b in range(NT):
+                    ref = _oracle_sweep(L, J[s], st[s, c, b], B[s, b], "hb", seed, s, c * NT + b, step0)
+                    for _ in range(2):
+                        ref = _oracle_sweep(L, J[s], ref, B[s, b], "or", seed, s, 0, 0)
+                    assert np.abs(out[s, c, b] - ref).max() <= 1e-11, (s, c, b)
+                    Hr = orc.energy(L, J[s], out[s, c, b])
+                    assert abs(H[s, c, b] - Hr) <= 1e-11 * max(1, abs(Hr))
+    eng.close()
+
+
 def test_policy_errors():
     from paper_1006_4247_gb300 import pt
     eng, J, B = make_engine(2, 1, 3, 2, "fp32")  # rows of one site: no resident kernel

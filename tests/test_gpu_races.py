@@ -19,8 +19,8 @@ those values and check that nothing else moves:
   neighbours (colour 1).
 
 Each case runs on the update path the engine picks for it (single-CTA
-resident, CTA-cluster resident, streaming with vector loads, streaming with
-bulk copies), checked through the launch counts."""
+resident, clusters of 1024- or 512-thread CTAs, streaming with vector loads,
+streaming with bulk copies), checked through the launch counts."""
 import os
 
 import numpy as np
@@ -53,8 +53,10 @@ CASES = [
     (32, "fp32", "streaming", {}, None),
     (20, "fp64", "streaming", {}, None),
     (32, "fp32", "streaming", {"PT_TMA": "1"}, None),
+    (32, "fp32", "auto", {"PT_CL_NARROW": "1"}, "resident"),
+    (24, "fp64", "auto", {"PT_CL_NARROW": "1"}, "resident"),
 ]
-IDS = [f"L{c[0]}-{c[1]}-{c[2]}" + ("-tma" if c[3] else "") for c in CASES]
+IDS = [f"L{c[0]}-{c[1]}-{c[2]}" + "".join("-" + k[3:].lower() for k in c[3]) for c in CASES]
 
 
 def _engine(L, precision, policy, env):
