@@ -202,6 +202,69 @@ def run_ladders(cases, n_cycles, n_burn, seed=0, mode="coolheat", n_copies=2):
     return out
 
 
+def feedback_kappa(cases, n_iter=10, block=300, kappa0=0.07, delta=0.35, step0=0.4, decay=0.75, n_burn=500,
+                   seed=0, mode="coolheat", n_copies=2, kappa_min=0.005):
+    """Per-pair cooling parameter by feedback on the measured acceptance, with
+    neither the network nor a scan (the paper notes that epsilon should
+    depend on the pair, Sec. 2.3 and Sec. 4).  Each case is (L, J, betas).
+
+    kappa_i = eps_i / ln(beta_{i+1}/beta_i) is tuned on a log scale.  The
+    chain is exact for every epsilon and the proposals of pair i depend on
+    eps_i alone, so all pairs of all samples are tuned at once in one
+    batched engine without re-equilibrating between settings: every
+    iteration runs `block` cycles with every ln kappa_i raised by `delta`
+    and `block` cycles with it lowered by `delta`, then moves ln kappa_i by
+    the current step towards the side whose acceptance (pooled over the
+    copies) was higher; the step shrinks by `decay` per iteration.
+    Returns (kappa per case [NT-1], history of the mean acceptance per
+    iteration, cycles spent)."""
+    Ls = [c[0] for c in cases]
+    Js = [np.asarray(c[1], np.float32) for c in cases]
+    Bs = [np.asarray(c[2], np.float64) for c in cases]
+    bounds = [eps_bound(L, J) for L, J in zip(Ls, Js)]
+    u = [np.full(len(B) - 1, math.log(kappa0)) for B in Bs]
+    n_or = np.array([max(1, (5 * L) // 4) for L in Ls], np.int32)
+    lo, hi = math.log(kappa_min), math.log(KAPPA_MAX)
+
+    def eps_of(shift):
+        return np.concatenate([eps_from_kappa(B, np.exp(np.clip(uu + shift, lo, hi)), bd)
+                               for B, uu, bd in zip(Bs, u, bounds)])
+
+    eng = pt.Engine(Ls, Js, Bs, n_copies=n_copies, seed=seed)
+    spent = 0
+
+    def block_acc(eps, n):
+        nonlocal spent
+        eng.set_params(None, eps)
+        p0, a0, _, _ = eng.stats()
+        eng.cycles(n, 1, int(n_or.max()), mode, n_or_samples=n_or)
+        p1, a1, _, _ = eng.stats()
+        spent += n
+        out, off = [], 0
+        for B in Bs:
+            m = n_copies * (len(B) - 1)
+            prop = (p1 - p0)[off:off + m].reshape(n_copies, -1).sum(0)
+            acc = (a1 - a0)[off:off + m].reshape(n_copies, -1).sum(0)
+            off += m
+            out.append(acc / np.maximum(prop, 1))
+        return out
+
+    hist = []
+    try:
+        block_acc(eps_of(0.0), n_burn)
+        step = step0
+        for _ in range(n_iter):
+            ap = block_acc(eps_of(+delta), block)
+            am = block_acc(eps_of(-delta), block)
+            for k in range(len(u)):
+                u[k] = np.clip(u[k] + step * np.sign(ap[k] - am[k]), lo, hi)
+            hist.append(float(np.mean([0.5 * (a + b).mean() for a, b in zip(ap, am)])))
+            step *= decay
+    finally:
+        eng.close()
+    return [np.exp(uu) for uu in u], hist, spent
+
+
 def training_targets(rows, n_cycles=1500, n_burn=500, seed=0, kappas=KAPPA_GRID, P=N_KNOTS):
     """Scan kappa on the geometric ladder of every row and derive its targets.
     Returns (features [B, 4], targets [B, 2P+1], info) with targets

@@ -125,3 +125,37 @@ def test_learned_ladder_against_geometric(trained):
     assert max(out["n_temps"]["learned_auto"]) <= NT
     # learned ladder + modified exchange: the plain method's round-trip rate with 30% fewer replicas
     assert out["learned_small"]["rt_per_chain"] >= out["plain_geometric"]["rt_per_chain"]
+
+
+def test_feedback_controller_reaches_scan_tuned_acceptance():
+    """Per-pair epsilon tuned online from the measured acceptance, with no
+    network and no scan (the ablation of the network's epsilon): started at
+    the low end of the scan grid, ten iterations of a sign controller reach
+    the acceptance of the scan-tuned kappa on the held-out samples."""
+    samples = [(EVAL_L, W.couplings(EVAL_L, 7000 + k)) for k in range(N_SAMPLES)]
+    NT = lad.default_n_temps(EVAL_L, *WINDOW)
+    geo = lad.geometric(*WINDOW, NT)
+    kap, hist, spent = lad.feedback_kappa([(L, J, geo) for L, J in samples], kappa0=lad.KAPPA_GRID[0], seed=51)
+    cases = []
+    for L, J in samples:
+        bd = lad.eps_bound(L, J)
+        cases += [(L, J, geo, lad.eps_from_kappa(geo, np.full(NT - 1, k), bd)) for k in lad.KAPPA_GRID]
+    for (L, J), k in zip(samples, kap):
+        cases.append((L, J, geo, lad.eps_from_kappa(geo, k, lad.eps_bound(L, J))))
+    res = lad.run_ladders(cases, 4000, 1000, seed=53)
+    nk = len(lad.KAPPA_GRID)
+    grid_acc = np.array([[res[s * nk + i][0].mean() for i in range(nk)] for s in range(N_SAMPLES)])  # [S, K]
+    best = int(np.argmax(grid_acc.mean(0)))
+    fb = np.array([res[N_SAMPLES * nk + s][0].mean() for s in range(N_SAMPLES)])
+    fb_min = np.array([res[N_SAMPLES * nk + s][0].min() for s in range(N_SAMPLES)])
+    scan_min = np.array([res[s * nk + best][0].min() for s in range(N_SAMPLES)])
+    out = {"kappa_grid": list(lad.KAPPA_GRID), "grid_acc": grid_acc.mean(0).round(4).tolist(),
+           "scan_kappa": lad.KAPPA_GRID[best], "feedback_kappa_mean": float(np.mean([k.mean() for k in kap])),
+           "feedback_acc": float(fb.mean()), "feedback_worst_pair": float(fb_min.mean()),
+           "scan_worst_pair": float(scan_min.mean()), "history": [round(h, 4) for h in hist],
+           "tuning_cycles": spent}
+    print("\nfeedback controller:", json.dumps(out))
+    assert fb.mean() >= 0.98 * grid_acc.mean(0)[best]        # the scan's acceptance without the scan
+    assert fb.mean() > grid_acc.mean(0)[0] + 0.01              # clearly above where it started
+    assert fb_min.mean() >= 0.95 * scan_min.mean()
+    assert hist[-1] > hist[0]
