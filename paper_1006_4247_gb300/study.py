@@ -133,14 +133,16 @@ def protocol(L, n_temps, n_sets=10, cycles=20000, burn=5000, kappa=0.1, seed0=80
     return out
 
 
-def replicas(L, n_temps_list, reference_nt, n_sets=10, cycles=20000, burn=5000, kappa=0.1, seed0=8000):
+def replicas(L, n_temps_list, reference_nt, n_sets=10, cycles=20000, burn=5000, kappa=0.1, seed0=8000,
+             plain_all=True):
     """Round-trip time against the number of replicas (the
     paper's reduced-N_T test generalised) for: the standard swap, decimation
     and cooling/heating on the geometric ladder (one kappa), and
     cooling/heating on the ladders and epsilons the learned network proposes
     for each set.  Returns t_R per (arm, N_T) (mean over sets, sweeps) and,
     per arm, the smallest N_T whose t_R is not above the standard method's at
-    reference_nt."""
+    reference_nt.  plain_all=False runs the standard swap at reference_nt
+    only (all the comparison needs)."""
     J = [workloads.couplings(L, seed0 + 97 * L + k) for k in range(n_sets)]
     spc = 1 + max(1, (5 * L) // 4)
     net = ladder.LearnedLadder.load()
@@ -152,7 +154,7 @@ def replicas(L, n_temps_list, reference_nt, n_sets=10, cycles=20000, burn=5000, 
         for nt in sorted(set(list(n_temps_list) + [reference_nt])):
             b = paper_ladder(nt)
             for arm in arms:
-                if arm == "plain" and nt != reference_nt and nt < min(n_temps_list):
+                if arm == "plain" and nt != reference_nt and (not plain_all or nt < min(n_temps_list)):
                     continue
                 mode = "coolheat" if arm.startswith("coolheat") else arm
                 eps = None
@@ -278,6 +280,8 @@ def main(argv=None):
     ap.add_argument("--kappa", type=float, default=0.1)
     ap.add_argument("--methods", default="plain,decimation,coolheat")
     ap.add_argument("--replicas", default="", help="comma-separated N_T list: run the replica-count study")
+    ap.add_argument("--plain-reference-only", action="store_true",
+                    help="replica study: the standard swap at the paper's N_T only")
     ap.add_argument("--equilibration", type=int, default=0, help="runs of the equilibration study (0: off)")
     ap.add_argument("--learned-large", action="store_true", help="learned ladder at L (e.g. 48) vs geometric")
     a = ap.parse_args(argv)
@@ -288,7 +292,8 @@ def main(argv=None):
         print(json.dumps(equilibration(a.L, nt, a.equilibration, a.cycles, a.kappa)))
     elif a.replicas:
         nts = [int(v) for v in a.replicas.split(",")]
-        print(json.dumps(replicas(a.L, nts, nt, a.sets, a.cycles, a.burn, a.kappa)))
+        print(json.dumps(replicas(a.L, nts, nt, a.sets, a.cycles, a.burn, a.kappa,
+                                  plain_all=not a.plain_reference_only)))
     else:
         print(json.dumps(protocol(a.L, nt, a.sets, a.cycles, a.burn, a.kappa, methods=tuple(a.methods.split(",")))))
 
