@@ -390,31 +390,34 @@ def ours(args):
                 "alg_bytes_per_launch": alg / n_launch, "avg_launch_us": pm["or"] / n_launch * 1e3}
 
     def resident_roofline(pm, ln, res_flags, steps):
-        """The resident block reads and writes each replica once per cycle; its
-        limit is the on-chip data path, reported against the FP32 issue rate
-        (152 SMs x 128 lanes x 2 FLOP x 2.07 GHz) with 60 FLOP counted per
-        site update."""
+        """The resident block reads and writes each replica once per cycle
+        through HBM and runs every half sweep out of shared memory: its
+        binding unit is the SM's shared-memory data path (ncu: l1tex near
+        83%), so that is the roofline reported.  Per 4-site vector an
+        overrelaxation update issues 24 16-byte shared-memory loads (own
+        spins 3, neighbour rows 15, couplings 6) and 3 16-byte stores: 108 B
+        per site update, against 152 SMs x 128 B/clock x 2.07 GHz.  The FP32
+        issue view (60 FLOP counted per update) and the streaming-equivalent
+        HBM rate are kept beside it."""
         upd = sum(w.n_copies * nt * L ** 3 * (w.n_hb + no)
                   for s, (L, nt, no) in enumerate(zip(w.L, w.n_replicas, nor)) if res_flags[s]) * steps
         if pm["resident"] <= 0 or upd == 0:
             return None
         t = pm["resident"] / 1e3
-        peak_alu = 152 * 128 * 2 * 2.07e9
         n_launch = max(ln["resident"], 1)
-        return {"bound": "alu", "achieved": upd * 60.0 / t / 1e12, "peak": peak_alu / 1e12, "unit": "TFLOP/s",
-                "frac": upd * 60.0 / t / peak_alu,
-                "traffic": ncu_traffic("k_resident", w.name, args.precision) if uniform else None,
+        peak_smem = 152 * 128 * 2.07e9
+        peak_alu = 152 * 128 * 2 * 2.07e9
+        traffic = ncu_traffic("k_resident", w.name, args.precision) if uniform else None
+        return {"bound": "smem", "achieved": upd * 108.0 / t / 1e12, "peak": peak_smem / 1e12, "unit": "TB/s",
+                "frac": upd * 108.0 / t / peak_smem, "traffic": traffic,
+                "traffic_note": "DRAM bytes per launch (ncu); the replica pool moves once each way per block",
                 "kernel": "k_resident / k_resident_cl (sweep block in shared memory, one CTA or a cluster)",
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz",
-                "alg_flops_per_launch": upd * 60.0 / n_launch, "avg_launch_us": t / n_launch * 1e6,
+                "peak_source": "derived: 152 SMs x 128 B/clock (shared-memory data path) x 2.07 GHz",
+                "alg_bytes_per_launch": upd * 108.0 / n_launch, "avg_launch_us": t / n_launch * 1e6,
                 "effective_hbm_GBps": upd * 36.4 / t / 1e9,
-                # the resident blocks' actual limit: the SM's shared-memory data path. Per 4-site
-                # vector an overrelaxation update issues 24 16-byte loads (own spins 3, neighbour
-                # rows 15, couplings 6) and 3 16-byte stores: 108 B per site update.
-                "onchip": {"bound": "shared-memory data path", "achieved": upd * 108.0 / t / 1e12,
-                           "peak": 152 * 128 * 2.07e9 / 1e12, "unit": "TB/s",
-                           "frac": upd * 108.0 / t / (152 * 128 * 2.07e9),
-                           "peak_source": "derived: 152 SMs x 128 B/clock x 2.07 GHz"}}
+                "alu": {"achieved": upd * 60.0 / t / 1e12, "peak": peak_alu / 1e12, "unit": "TFLOP/s",
+                        "frac": upd * 60.0 / t / peak_alu,
+                        "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz, 60 FLOP per update"}}
 
     dominant = max(("or", "resident"), key=lambda k: prof_ms.get(k, 0.0))
     share = {k: v / max(sum(prof_ms.values()), 1e-9) for k, v in prof_ms.items()}

@@ -18,6 +18,7 @@
 #include <cooperative_groups.h>
 
 #include "kernels.h"
+#include "exchange_common.cuh"
 #include "pt_device.cuh"
 
 namespace cg = cooperative_groups;

@@ -13,6 +13,7 @@
 // into the buffer of the configuration it replaces, and the
 // temperature-to-buffer map records where each configuration lives.
 #include "kernels.h"
+#include "exchange_common.cuh"
 #include "pt_device.cuh"
 
 namespace ptk {
