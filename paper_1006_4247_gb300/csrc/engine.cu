@@ -119,6 +119,7 @@ struct pt_engine {
     // event of a buffer marks the end of its last copy)
     struct Staging { void* host = nullptr; size_t bytes = 0; cudaEvent_t ev = nullptr; };
     Staging stage[2];
+    int* err_host = nullptr;          // pinned copy of the device error word (read by sync)
     int stage_next = 0;
     // captured update cycle (pt_cycles)
     cudaGraph_t graph = nullptr;
@@ -172,6 +173,8 @@ struct pt_engine {
             if (st.ev) cudaEventDestroy(st.ev);
             st = Staging();
         }
+        if (err_host) cudaFreeHost(err_host);
+        err_host = nullptr;
         if (graph_exec) cudaGraphExecDestroy(graph_exec);
         if (graph) cudaGraphDestroy(graph);
         graph_exec = nullptr;
@@ -648,9 +651,11 @@ pt_status create_impl(pt_handle* out, int n_samples, const int* Ls, const int* N
 // Synchronise the engine's stream; report a bounded device-side wait that
 // gave up since the last check (the error word is cleared).
 pt_status sync(pt_engine* e) {
+    // the error word rides on the stream behind the work, so one wait covers both
+    if (!e->err_host) CK(cudaMallocHost((void**)&e->err_host, sizeof(int)));
+    CK(cudaMemcpyAsync(e->err_host, e->d.err, sizeof(int), cudaMemcpyDeviceToHost, e->stream));
     CK(e->stream ? cudaStreamSynchronize(e->stream) : cudaDeviceSynchronize());
-    int err = 0;
-    CK(cudaMemcpy(&err, e->d.err, sizeof(int), cudaMemcpyDeviceToHost));
+    const int err = *e->err_host;
     if (err) {
         const int zero = 0;
         CK(cudaMemcpy(e->d.err, &zero, sizeof(int), cudaMemcpyHostToDevice));
