@@ -136,8 +136,11 @@ __global__ void k_advance_step(unsigned long long* d_step, int by) { *d_step += 
 // beta index (Eq. over) and chi = (1/N) sum_ab Q_ab^2.  One block per
 // (sample, beta index); each thread reads 16-byte vectors of consecutive sites
 // (a vector never straddles the two colours: half is a multiple of 4) and
-// accumulates them in T in chunks of at most 32 sites, then in double; warp
-// shuffles and one shared-memory pass finish the nine sums in a fixed order.
+// accumulates them in T in chunks of at most 32 sites; the chunk sums are
+// added in T with compensation (Knuth's two-sum), which keeps the thread's
+// total as accurate as a double sum rounded to T without work on GB300's slow
+// FP64 pipe; warp shuffles and one shared-memory pass finish the nine sums
+// in a fixed order.
 template <typename T>
 __global__ void __launch_bounds__(TILE) k_overlap(DevBatch a) {
     __shared__ double sh[9 * 32];
@@ -149,9 +152,9 @@ __global__ void __launch_bounds__(TILE) k_overlap(DevBatch a) {
     const int r0 = sd.r0 + b, r1 = sd.r0 + sd.NT + b;
     const T* b0 = (const T*)a.spins + a.chain_off[sd.chain0] + (long long)a.bufmap[r0] * (6LL * half);
     const T* b1 = (const T*)a.spins + a.chain_off[sd.chain0 + 1] + (long long)a.bufmap[r1] * (6LL * half);
-    double acc[9];
+    T hi[9], lo[9];
 #pragma unroll
-    for (int n = 0; n < 9; ++n) acc[n] = 0.0;
+    for (int n = 0; n < 9; ++n) hi[n] = lo[n] = (T)0;
     constexpr int V = 16 / sizeof(T);
     constexpr int CH = 32 / V;  // vectors per chunk of 32 sites
     const int N = 2 * half, NV = N / V;
@@ -178,13 +181,18 @@ __global__ void __launch_bounds__(TILE) k_overlap(DevBatch a) {
                 for (int v = 0; v < V; ++v) part[n] += u0[n / 3][v] * u1[n % 3][v];
         }
 #pragma unroll
-        for (int n = 0; n < 9; ++n) acc[n] += (double)part[n];
+        for (int n = 0; n < 9; ++n) {
+            const T sum = hi[n] + part[n];
+            const T bb = sum - hi[n];
+            lo[n] += (hi[n] - (sum - bb)) + (part[n] - bb);
+            hi[n] = sum;
+        }
     }
-    // the thread totals (double over chunks) enter the warp tree in T, the
-    // warp sums are added in double (the precision policy of all reductions)
+    // the thread totals enter the warp tree in T, the warp sums are added in
+    // double (the precision policy of all reductions)
     T tp[9];
 #pragma unroll
-    for (int n = 0; n < 9; ++n) tp[n] = (T)acc[n];
+    for (int n = 0; n < 9; ++n) tp[n] = hi[n] + lo[n];
     double tot[9];
     block_sum_multi<T, 9>(tp, tot, sh);
     if (threadIdx.x == 0) {
