@@ -165,25 +165,32 @@ __device__ __forceinline__ T decim_D(T n, T b1, T b2, T db, T lr) {
 // ---------------------------------------------------------------------------
 template <typename T, int V>
 __device__ __forceinline__ void decimation_chain(const DevBatch& a, cg::cluster_group& cl, ChainSmem& sm,
-                                                 const DecimPairs<T, MAX_NT>& dp, const ChainDesc& cd,
-                                                 const SampleDesc& sd, int ch, int cs, int rank);
+                                                 const DecimPairs<T, MAX_NT>& dp, PairDraws<MAX_NT>& pd,
+                                                 const ChainDesc& cd, const SampleDesc& sd, int ch, int cs,
+                                                 int rank);
 
 template <typename T>
 __global__ void __launch_bounds__(EX_THREADS, 2) k_exchange_decimation(DevBatch a) {
     __shared__ ChainSmem sm;
     __shared__ DecimPairs<T, MAX_NT> dp;
+    __shared__ PairDraws<MAX_NT> pd;
     cg::cluster_group cl = cg::this_cluster();
     const int cs = (int)cl.num_blocks(), rank = (int)cl.block_rank();
     const int ch = blockIdx.x / cs;
     const ChainDesc cd = a.chains[ch];
     const SampleDesc& sd = a.samples[cd.s];
     const int NT = sd.NT, half = sd.half;
-    dp.load(a.betas + sd.beta_off, NT);  // visible after load_chain's barrier
+    dp.load(a.betas + sd.beta_off, NT);  // both visible after load_chain's barrier
+    pd.load(a.seed, (uint32_t)cd.s, (uint32_t)cd.copy, *a.d_step, NT - 1);
     load_chain(a, cd, NT, sm, ch);
-    if (sd.vec == 4) decimation_chain<T, (sizeof(T) == 4 ? 4 : 2)>(a, cl, sm, dp, cd, sd, ch, cs, rank);
-    else if (sd.vec == 2) decimation_chain<T, 2>(a, cl, sm, dp, cd, sd, ch, cs, rank);
-    else decimation_chain<T, 1>(a, cl, sm, dp, cd, sd, ch, cs, rank);
-    if (rank == 0) store_chain(a, cd, NT, sm, ch);
+    if (sd.vec == 4) decimation_chain<T, (sizeof(T) == 4 ? 4 : 2)>(a, cl, sm, dp, pd, cd, sd, ch, cs, rank);
+    else if (sd.vec == 2) decimation_chain<T, 2>(a, cl, sm, dp, pd, cd, sd, ch, cs, rank);
+    else decimation_chain<T, 1>(a, cl, sm, dp, pd, cd, sd, ch, cs, rank);
+    if (rank == 0) {
+        store_chain(a, cd, NT, sm, ch);
+        __syncthreads();  // thread 0's per-pair counts
+        pd.store(a.prop + cd.pair_off, a.acc + cd.pair_off, NT - 1);
+    }
     cl.sync();  // no CTA leaves while others may still read its shared memory
 }
 
@@ -191,8 +198,9 @@ __global__ void __launch_bounds__(EX_THREADS, 2) k_exchange_decimation(DevBatch 
 // vectors of the decimated colour (16-byte loads of the neighbour rows).
 template <typename T, int V>
 __device__ __forceinline__ void decimation_chain(const DevBatch& a, cg::cluster_group& cl, ChainSmem& sm,
-                                                 const DecimPairs<T, MAX_NT>& dp, const ChainDesc& cd,
-                                                 const SampleDesc& sd, int ch, int cs, int rank) {
+                                                 const DecimPairs<T, MAX_NT>& dp, PairDraws<MAX_NT>& pd,
+                                                 const ChainDesc& cd, const SampleDesc& sd, int ch, int cs,
+                                                 int rank) {
     const int NT = sd.NT, half = sd.half;
     int lo, hi;
     slice(half / V, rank, cs, lo, hi);  // in vectors
@@ -227,14 +235,10 @@ __device__ __forceinline__ void decimation_chain(const DevBatch& a, cg::cluster_
         cluster_sum<T, 1>(cl, sm, part, pub);
         if (threadIdx.x == 0) {
             const double lnA = sm.sum[0];
-            const uint4 w = rng_words(a.seed, (uint32_t)cd.s, (uint32_t)i, (uint32_t)cd.copy, step, 1u);
-            const bool ok = metropolis(lnA, u53(w.x, w.y));
+            const bool ok = metropolis(lnA, pd.u[i]);
             sm.flag = ok;
-            if (rank == 0) {
-                a.prop[cd.pair_off + i] += 1;
-                if (ok) a.acc[cd.pair_off + i] += 1;
-            }
             if (ok) {
+                pd.acc[i] = 1;
                 int t = sm.buf[i]; sm.buf[i] = sm.buf[i + 1]; sm.buf[i + 1] = t;
                 t = sm.lab[i]; sm.lab[i] = sm.lab[i + 1]; sm.lab[i + 1] = t;
             }

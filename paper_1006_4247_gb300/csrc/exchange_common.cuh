@@ -24,4 +24,30 @@ struct DecimPairs {
     }
 };
 
+// The parts of a chain's tempering update that do not depend on the walk's
+// decisions, prepared by the whole block before the walk so that the one
+// thread that decides each pair waits on neither memory nor Philox: the
+// uniform of every pair (purpose 1, c0 = pair, c1 = copy; the same numbers
+// the decision would draw) and a per-pair count of acceptances, added to the
+// global counters once after the walk.
+template <int N>
+struct PairDraws {
+    double u[N];
+    int acc[N];
+    __device__ void load(uint64_t seed, uint32_t sample, uint32_t copy, unsigned long long step, int n_pairs) {
+        for (int i = (int)threadIdx.x; i < n_pairs; i += (int)blockDim.x) {
+            const uint4 w = rng_words(seed, sample, (uint32_t)i, copy, step, 1u);
+            u[i] = u53(w.x, w.y);
+            acc[i] = 0;
+        }
+    }
+    // every pair was proposed once; the caller synchronises the block first
+    __device__ void store(long long* prop, long long* accg, int n_pairs) const {
+        for (int i = (int)threadIdx.x; i < n_pairs; i += (int)blockDim.x) {
+            prop[i] += 1;
+            accg[i] += acc[i];
+        }
+    }
+};
+
 }  // namespace ptk

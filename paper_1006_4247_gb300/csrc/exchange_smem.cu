@@ -170,18 +170,27 @@ template <typename T>
 __global__ void __launch_bounds__(SX_THREADS, 1) k_exchange_coolheat_smem(DevBatch a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ SxSmem sm;
+    __shared__ PairDraws<SX_MAX_NT> pd;
+    __shared__ double pHH[SX_MAX_NT], pLJ[SX_MAX_NT], pbeta[SX_MAX_NT];  // per pair / replica
     const int ch = blockIdx.x;
     const ChainDesc cd = a.chains[ch];
     const SampleDesc& sd = a.samples[cd.s];
     const int NT = sd.NT, half = sd.half, n3 = 6 * half;
     T* const slots = reinterpret_cast<T*>(smem_raw);
     auto slot = [&](int q) { return slots + (size_t)q * n3; };
-    sx_load_state(a, cd, NT, sm);
+    const unsigned long long step = *a.d_step;
+    pd.load(a.seed, (uint32_t)cd.s, (uint32_t)cd.copy, step, NT - 1);
+    for (int q = (int)threadIdx.x; q < NT; q += (int)blockDim.x) {
+        pbeta[q] = a.betas[sd.beta_off + q];
+        if (q + 1 < NT) {
+            pHH[q] = a.heat_H[cd.pair_off + q];
+            pLJ[q] = a.heat_lnJ[cd.pair_off + q];
+        }
+    }
+    sx_load_state(a, cd, NT, sm);  // its barrier also publishes the tables above
     T* pool = (T*)a.spins + a.chain_off[ch];
     const float* J0 = a.J + sd.J_off;
     const float* J1 = a.J + sd.J_off + 3 * half;
-    const unsigned long long step = *a.d_step;
-    const double* beta = a.betas + sd.beta_off;
     const bool v2 = (sd.hL % 2) == 0;
     int A = 0;               // slot of s1
     int ownerA = sm.buf[0];  // global buffer of s1
@@ -206,15 +215,13 @@ __global__ void __launch_bounds__(SX_THREADS, 1) k_exchange_coolheat_smem(DevBat
         const long long pair = cd.pair_off + i;
         if (threadIdx.x == 0) {
             const double LJ1 = tot[0], HC = tot[1];
-            const double HH = a.heat_H[pair], LJ2 = a.heat_lnJ[pair];
-            const double b1 = beta[i], b2 = beta[i + 1];
+            const double HH = pHH[i], LJ2 = pLJ[i];
+            const double b1 = pbeta[i], b2 = pbeta[i + 1];
             const double lnA = -b2 * HC - b1 * HH + b1 * sm.H[i] + b2 * sm.H[i + 1] + LJ1 - LJ2;
-            const uint4 w = rng_words(a.seed, (uint32_t)cd.s, (uint32_t)i, (uint32_t)cd.copy, step, 1u);
-            const bool ok = sx_metropolis(lnA, u53(w.x, w.y));
-            a.prop[cd.pair_off + i] += 1;
+            const bool ok = sx_metropolis(lnA, pd.u[i]);
             sm.flag = ok;
             if (ok) {
-                a.acc[cd.pair_off + i] += 1;
+                pd.acc[i] = 1;
                 sm.H[i] = HH;
                 sm.H[i + 1] = HC;
                 const int t = sm.lab[i]; sm.lab[i] = sm.lab[i + 1]; sm.lab[i + 1] = t;
@@ -238,6 +245,7 @@ __global__ void __launch_bounds__(SX_THREADS, 1) k_exchange_coolheat_smem(DevBat
     }
     if (dirtyA) sx_copy(pool + (long long)ownerA * n3, slot(A), n3);
     sx_store_state(a, cd, NT, sm, ch);
+    pd.store(a.prop + cd.pair_off, a.acc + cd.pair_off, NT - 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -252,16 +260,18 @@ __global__ void __launch_bounds__(SX_THREADS, 1) k_exchange_decimation_smem(DevB
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ SxSmem sm;
     __shared__ DecimPairs<T, SX_MAX_NT> dp;
+    __shared__ PairDraws<SX_MAX_NT> pd;
     const int ch = blockIdx.x;
     const ChainDesc cd = a.chains[ch];
     const SampleDesc& sd = a.samples[cd.s];
     const int NT = sd.NT, half = sd.half, n3 = 6 * half;
     T* const slots = reinterpret_cast<T*>(smem_raw);
     auto slot = [&](int q) { return slots + (size_t)q * n3; };
-    dp.load(a.betas + sd.beta_off, NT);  // visible after sx_load_state's barrier
+    const unsigned long long step = *a.d_step;
+    dp.load(a.betas + sd.beta_off, NT);  // both visible after sx_load_state's barrier
+    pd.load(a.seed, (uint32_t)cd.s, (uint32_t)cd.copy, step, NT - 1);
     sx_load_state(a, cd, NT, sm);
     T* pool = (T*)a.spins + a.chain_off[ch];
-    const unsigned long long step = *a.d_step;
     const uint4 wd = rng_words(a.seed, (uint32_t)cd.s, 0u, (uint32_t)cd.copy, step, 3u);
     const int d0 = (int)(wd.x & 1u);
     int A = 0;
@@ -291,12 +301,10 @@ __global__ void __launch_bounds__(SX_THREADS, 1) k_exchange_decimation_smem(DevB
         block_sum_multi<T, 1>(part, tot1, sm.red);
         const double lnA = tot1[0];
         if (threadIdx.x == 0) {
-            const uint4 w = rng_words(a.seed, (uint32_t)cd.s, (uint32_t)i, (uint32_t)cd.copy, step, 1u);
-            const bool ok = sx_metropolis(lnA, u53(w.x, w.y));
-            a.prop[cd.pair_off + i] += 1;
+            const bool ok = sx_metropolis(lnA, pd.u[i]);
             sm.flag = ok;
             if (ok) {
-                a.acc[cd.pair_off + i] += 1;
+                pd.acc[i] = 1;
                 sm.buf[i] = ownerB;
                 sm.buf[i + 1] = ownerA;
                 const int t = sm.lab[i]; sm.lab[i] = sm.lab[i + 1]; sm.lab[i + 1] = t;
@@ -340,13 +348,15 @@ __global__ void __launch_bounds__(SX_THREADS, 1) k_exchange_decimation_smem(DevB
     }
     if (dirtyA) sx_copy(pool + (long long)ownerA * n3, slot(A), n3);
     sx_store_state(a, cd, NT, sm, ch);
+    pd.store(a.prop + cd.pair_off, a.acc + cd.pair_off, NT - 1);
 }
 
 // Two slots of one configuration each (s1 and its transform, or the pair).
 size_t exchange_smem_bytes(int mode, int half, bool fp64) { return (size_t)2 * 6 * half * (fp64 ? 8 : 4); }
 
 bool exchange_smem_supported(int mode, int max_half, bool fp64) {
-    return (mode == 1 || mode == 2) && exchange_smem_bytes(mode, max_half, fp64) <= 200 * 1024;
+    // dynamic slots plus about 30 KB of static per-chain tables within the 227 KB of a CTA
+    return (mode == 1 || mode == 2) && exchange_smem_bytes(mode, max_half, fp64) <= 196 * 1024;
 }
 
 cudaError_t launch_exchange_smem(const DevBatch& b, bool fp64, int mode, int max_half, cudaStream_t st) {

@@ -481,13 +481,16 @@ __device__ __forceinline__ double warp_sum(double v) {
 // T over its few sites: the 32 lanes of a warp are added in T, the warp sums
 // in double (so float work stays on the float pipes and at most 32 float
 // terms meet before the sum is carried in double).  One pass, two barriers;
-// results valid in warp 0.  sh must hold NV * 32 doubles.  With few warps
-// and many values the warp sums of value k are added by lane k in warp order
-// (nw dependent double adds on NV lanes), else by a shuffle tree per value
-// (5 NV double adds): whichever issues fewer instructions to the FP64 pipe.
+// results valid in warp 0.  sh must hold NV * 32 doubles.  The warp sums
+// are stored in T and widened by warp 0 (one conversion per value and lane
+// instead of one per warp and value); with few warps and many values the
+// warp sums of value k are then added by lane k in warp order (nw dependent
+// double adds on NV lanes), else by a shuffle tree per value (5 NV double
+// adds): whichever issues fewer instructions to GB300's slow FP64 pipe.
 template <typename T, int NV>
 __device__ __forceinline__ void block_sum_multi(const T (&v)[NV], double (&out)[NV], double* sh) {
     static_assert(NV <= 32, "one lane per value");
+    T* shT = reinterpret_cast<T*>(sh);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     __syncthreads();
 #pragma unroll
@@ -495,21 +498,21 @@ __device__ __forceinline__ void block_sum_multi(const T (&v)[NV], double (&out)[
         T x = v[k];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xFFFFFFFFu, x, o);
-        if (lane == 0) sh[k * 32 + wid] = (double)x;
+        if (lane == 0) shT[k * 32 + wid] = x;
     }
     __syncthreads();
     const int nw = (blockDim.x + 31) >> 5;
     if (wid == 0) {
-        if (nw < 5 * NV) {
+        if (2 * nw < 6 * NV) {
             double r = 0.0;
             if (lane < NV)
-                for (int w = 0; w < nw; ++w) r += sh[lane * 32 + w];
+                for (int w = 0; w < nw; ++w) r += (double)shT[lane * 32 + w];
 #pragma unroll
             for (int k = 0; k < NV; ++k) out[k] = __shfl_sync(0xFFFFFFFFu, r, k);
         } else {
 #pragma unroll
             for (int k = 0; k < NV; ++k) {
-                double r = (lane < nw) ? sh[k * 32 + lane] : 0.0;
+                double r = (lane < nw) ? (double)shT[k * 32 + lane] : 0.0;
                 out[k] = warp_sum(r);
             }
         }
