@@ -194,11 +194,12 @@ def oracle_cycle_rate(w, budget_s=12.0, max_cycles=None):
     B = W.linear_betas(NT, w.beta_min, w.beta_max)
     run = oracle.Run(L, J, B, n_copies=w.n_copies, seed=1, eps=w.eps)
     mode = {"plain": 0, "decimation": 1, "coolheat": 2}[w.exchange]
-    per_cycle = w.n_copies * NT * L ** 3 * (w.n_hb + w.n_or)
+    nor0 = n_or_of(w)[0]  # the sample's own count (5L/4 in an uneven batch)
+    per_cycle = w.n_copies * NT * L ** 3 * (w.n_hb + nor0)
     t0 = time.perf_counter()
     n = 0
     while True:
-        run.cycles(1, w.n_hb, w.n_or, mode, record=False)
+        run.cycles(1, w.n_hb, nor0, mode, record=False)
         n += 1
         el = time.perf_counter() - t0
         if el >= budget_s or (max_cycles and n >= max_cycles):
@@ -209,19 +210,17 @@ def oracle_cycle_rate(w, budget_s=12.0, max_cycles=None):
 def _oracle_worker(job):
     """One host process of the all-cores oracle leg: sample k of the workload
     (its own couplings), cycles for `budget_s` seconds; returns site updates."""
-    name, k, budget_s = job
+    (L, NT, j_seed, beta_min, beta_max, n_copies, eps, exchange, n_hb, n_or), k, budget_s = job
     import oracle
-    w = W.WORKLOADS[name]()
-    L, NT = w.L[0], w.n_replicas[0]
-    J = W.couplings(L, w.j_seed0 + k).astype(np.float64)
-    B = W.linear_betas(NT, w.beta_min, w.beta_max)
-    run = oracle.Run(L, J, B, n_copies=w.n_copies, seed=1 + k, eps=w.eps)
-    mode = {"plain": 0, "decimation": 1, "coolheat": 2}[w.exchange]
-    per_cycle = w.n_copies * NT * L ** 3 * (w.n_hb + w.n_or)
+    J = W.couplings(L, j_seed + k).astype(np.float64)
+    B = W.linear_betas(NT, beta_min, beta_max)
+    run = oracle.Run(L, J, B, n_copies=n_copies, seed=1 + k, eps=eps)
+    mode = {"plain": 0, "decimation": 1, "coolheat": 2}[exchange]
+    per_cycle = n_copies * NT * L ** 3 * (n_hb + n_or)
     t0 = time.perf_counter()
     n = 0
     while time.perf_counter() - t0 < budget_s:
-        run.cycles(1, w.n_hb, w.n_or, mode, record=False)
+        run.cycles(1, n_hb, n_or, mode, record=False)
         n += 1
     return per_cycle * n
 
@@ -242,10 +241,12 @@ def oracle_rate_all_cores(w, budget_s=12.0):
     oracle.build()
     n = host_cores()
     ctx = mp.get_context("spawn")
+    spec = (w.L[0], w.n_replicas[0], w.j_seed0, w.beta_min, w.beta_max, w.n_copies, w.eps, w.exchange,
+            w.n_hb, n_or_of(w)[0])  # the sample the single-thread leg times, other couplings per process
     with ctx.Pool(n) as pool:
-        pool.map(_oracle_worker, [(w.name, k, 0.2) for k in range(n)])  # interpreters started and warm
+        pool.map(_oracle_worker, [(spec, k, 0.2) for k in range(n)])  # interpreters started and warm
         t0 = time.perf_counter()
-        ups = pool.map(_oracle_worker, [(w.name, k, budget_s) for k in range(n)])
+        ups = pool.map(_oracle_worker, [(spec, k, budget_s) for k in range(n)])
         el = time.perf_counter() - t0
     return sum(ups) / (el * 1e9), n, el
 
@@ -262,12 +263,13 @@ def reference_arm(args):
     B = W.linear_betas(NT, w.beta_min, w.beta_max)
     run = oracle.Run(L, J, B, n_copies=w.n_copies, seed=1, eps=w.eps)
     mode = {"plain": 0, "decimation": 1, "coolheat": 2}[w.exchange]
+    nor0 = n_or_of(w)[0]
     for _ in range(args.warmup):
-        run.cycles(1, w.n_hb, w.n_or, mode, record=False)
-    per_step = w.n_copies * NT * L ** 3 * (w.n_hb + w.n_or)
+        run.cycles(1, w.n_hb, nor0, mode, record=False)
+    per_step = w.n_copies * NT * L ** 3 * (w.n_hb + nor0)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        run.cycles(1, w.n_hb, w.n_or, mode, record=True)
+        run.cycles(1, w.n_hb, nor0, mode, record=True)
     el = time.perf_counter() - t0
     v = per_step * args.steps / (el * 1e9)
     sample = f"one sample (L={L}, {NT} replicas x {w.n_copies} copies) of {w.name}, one cycle per step"
@@ -277,7 +279,7 @@ def reference_arm(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "impl": "reference",
         "config": {"workload": w.name, "L": L, "replicas": NT, "copies": w.n_copies,
-                   "samples": 1, "n_hb": w.n_hb, "n_or": w.n_or, "exchange": w.exchange},
+                   "samples": 1, "n_hb": w.n_hb, "n_or": nor0, "exchange": w.exchange},
         "cpu_baseline": {"value": v, "unit": "updates/ns", "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": "updates/ns", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
