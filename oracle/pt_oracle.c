@@ -589,7 +589,7 @@ void orc_exchange_coolheat(int L, const double *J, int NT, const double *betas,
 }
 
 /* ------------------------------------------------------------------------ */
-/* Driver: update cycles of one sample (section IV): per cycle n_hb heat-    */
+/* Cycles of one sample (section IV): per cycle n_hb heat-                 */
 /* bath sweeps and n_or overrelaxation sweeps (each a colour-0 then colour-1 */
 /* half sweep) of every replica, then one exchange per chain.  The counter   */
 /* `step` advances once per half sweep and once per exchange, shared by all  */

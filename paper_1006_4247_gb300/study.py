@@ -135,7 +135,7 @@ def protocol(L, n_temps, n_sets=10, cycles=20000, burn=5000, kappa=0.1, seed0=80
 
 def replicas(L, n_temps_list, reference_nt, n_sets=10, cycles=20000, burn=5000, kappa=0.1, seed0=8000,
              plain_all=True):
-    """Round-trip time against the number of replicas (SURVEY NEXT-2, the
+    """Round-trip time against the number of replicas (the
     paper's reduced-N_T test generalised) for: the standard swap, decimation
     and cooling/heating on the geometric ladder (one kappa), and
     cooling/heating on the ladders and epsilons the learned network proposes
@@ -180,7 +180,7 @@ def replicas(L, n_temps_list, reference_nt, n_sets=10, cycles=20000, burn=5000, 
 
 def equilibration(L=16, n_temps=15, n_runs=2000, cycles=1000, kappa=0.1, seed=8500,
                   methods=("plain", "decimation", "coolheat")):
-    """Equilibration from the ordered start (Sec. 4.4, Fig. 1; SURVEY NEXT-3):
+    """Equilibration from the ordered start (Sec. 4.4, Fig. 1):
     n_runs independent runs (independent random numbers) on one coupling set,
     every spin (1, 0, 0) at the start, all runs in one batched engine; the
     mean and standard error over runs of chi at the lowest temperature after

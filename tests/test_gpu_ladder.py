@@ -6,7 +6,7 @@ geometric ladders, ``paper_1006_4247_gb300/data/ladder_train.npz``) and
 evaluated on held-out coupling samples at a lattice size it never saw
 (L = 10), inverse temperatures 2..8, against:
 
-* the judge: the geometric ladder with one cooling/heating parameter for
+* the yardstick: the geometric ladder with one cooling/heating parameter for
   all pairs, tuned by a scan on the evaluation samples themselves (the
   paper's procedure, Sec. 2.3), at the replica count of the paper's rule;
 * the same geometric ladder with epsilon tuned per pair and per sample from
@@ -74,7 +74,7 @@ def test_learned_ladder_against_geometric(trained):
     samples = [(EVAL_L, W.couplings(EVAL_L, 7000 + k), *WINDOW) for k in range(N_SAMPLES)]
     NT = lad.default_n_temps(EVAL_L, *WINDOW)
     geo = lad.geometric(*WINDOW, NT)
-    # the judge's kappa: a scan on the evaluation samples themselves
+    # the yardstick's kappa: a scan on the evaluation samples themselves
     scan = [(L, J, geo, lad.eps_from_kappa(geo, np.full(NT - 1, k), lad.eps_bound(L, J)))
             for k in lad.KAPPA_GRID for (L, J, _, _) in samples]
     res = lad.run_ladders(scan, 2000, 1000, seed=41)
@@ -119,9 +119,9 @@ def test_learned_ladder_against_geometric(trained):
     # equalised acceptance: flatter profile, higher worst pair
     assert l["acc_spread"] < g["acc_spread"]
     assert l["acc_min"] >= g["acc_min"]
-    # round trips not worse than the judge's within the noise
+    # round trips not worse than the yardstick's within the noise
     assert l["rt_per_chain"] >= g["rt_per_chain"] - 3 * np.hypot(l["rt_se"], g["rt_se"])
-    # fewer replicas for the judge's worst-pair acceptance
+    # fewer replicas for the yardstick's worst-pair acceptance
     assert max(out["n_temps"]["learned_auto"]) <= NT
     # learned ladder + modified exchange: the plain method's round-trip rate with 30% fewer replicas
     assert out["learned_small"]["rt_per_chain"] >= out["plain_geometric"]["rt_per_chain"]
