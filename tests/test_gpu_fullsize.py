@@ -1,10 +1,16 @@
 """Parity at the benchmark's full sizes, in the launch configuration bench.py
 times, on sampled outputs the oracle computes one by one:
 
-  L = 16, 64 samples x 24 replicas x 2 copies, float (shared-memory resident
-  sweep kernel, staged cooling/heating exchange);
-  L = 32, 16 samples x 48 replicas x 2 copies, float (streaming half sweeps,
-  cluster decimation exchange).
+  L = 16, 64 samples x 24 replicas x 2 copies, float (one CTA per replica in
+  shared memory, staged cooling/heating exchange);
+  L = 32, 16 samples x 48 replicas x 2 copies, float (clusters of CTAs per
+  replica, narrow ones of 8 CTAs where the autotuner picks them as it does on
+  GB300; cluster decimation exchange);
+  the uneven batch of 256 samples, L from {8, 12, 16, 24, 32}, 5L/4
+  overrelaxation sweeps per sample (one CTA or narrow clusters by size).
+
+The engines run the autotuner first, as bench.py does, so the paths checked
+are the ones it times (the tests assert which).
 
 Checked per sampled replica: one heat-bath sweep and one overrelaxation sweep
 site by site (the second half sweep from the engine's first-half result, as
@@ -36,7 +42,13 @@ def _engine(name):
     eng = pt.Engine(w.L[0], J, B, n_copies=2, precision="fp32", seed=7)
     eps = np.concatenate([np.full(n - 1, w.eps, np.float32) for n in w.n_replicas])
     eng.set_params(eps=eps)
+    eng.autotune(w.n_hb, w.n_or)
     return w, eng, J.astype(np.float64), B
+
+
+# resident paths (pt_get_paths codes >= 10) at both sizes; at L = 32 the
+# autotuner's pick between wide and narrow clusters is the one checked
+EXPECTED_PATH = {"L16_R24_S64": (10,), "L32_R48_S16": (10, 20)}
 
 
 def _check_half_sweeps(L, J, before, after, kind, beta, seed, sample, rep_id, step0):
@@ -67,6 +79,8 @@ def test_fullsize_sweeps_sampled(name, samples):
     w, eng, J, B = _engine(name)
     L = w.L[0]
     NT = w.n_replicas[0]
+    choice, _ = eng.paths()
+    assert all(c // 10 * 10 in EXPECTED_PATH[name] for c in choice), choice
     eng.sweep(w.n_hb, w.n_or)          # one cycle exactly as the benchmark runs it
     eng.exchange(w.exchange)
     for kind, (nh, no) in (("hb", (1, 0)), ("or", (0, 1))):
@@ -123,4 +137,44 @@ def test_fullsize_exchange_sampled(name, chains):
     # float and double decisions differ only where ln A is within float
     # round-off of ln u; at most one sampled chain may show such a tie
     assert mismatched <= max(0, len(chains) - 1)
+    eng.close()
+
+
+def test_fullsize_uneven_batch_sampled():
+    """The uneven batch as bench.py runs it (autotuned paths, per-sample
+    overrelaxation counts, plain swap): one heat-bath and one overrelaxation
+    sweep checked site by site for replicas of every lattice size, on the
+    resident kernel each size uses."""
+    w = W.uneven_batch()
+    Js = w.couplings()
+    Bs = w.betas()
+    eng = pt.Engine(list(w.L), Js, Bs, n_copies=2, precision="fp32", seed=7)
+    nor = [w.extra["n_or_per_L"][L] for L in w.L]
+    eng.autotune(w.n_hb, max(nor))
+    choice, ctas = eng.paths()
+    assert (choice >= 10).all()                           # every sample resident
+    picks = {}
+    for s, L in enumerate(w.L):
+        picks.setdefault(L, s)
+    for L, s in picks.items():
+        assert (ctas[s] == 1) == (L <= 16), (L, ctas[s])  # clusters only above L = 16
+    eng.sweep_samples(w.n_hb, nor)
+    eng.exchange(w.exchange)
+    off = np.concatenate([[0], np.cumsum([2 * n for n in w.n_replicas])])
+    for kind, (nh, no) in (("hb", (1, 0)), ("or", (0, 1))):
+        tags = [(s, c, b) for s in picks.values() for (c, b) in ((0, 0), (1, w.n_replicas[s] - 1))]
+        before = {t: eng.get_spins(*t) for t in tags}
+        step0 = eng.step
+        eng.sweep_samples(nh, [no] * len(w.L))
+        for (s, c, b) in tags:
+            L, NT = w.L[s], w.n_replicas[s]
+            after = eng.get_spins(s, c, b)
+            _check_half_sweeps(L, np.asarray(Js[s], np.float64), before[(s, c, b)], after, kind, Bs[s][b], 7, s,
+                               c * NT + b, step0)
+            assert np.allclose(np.linalg.norm(after, axis=1), 1.0, atol=1e-5)
+    H = eng.energies()
+    for (s, c, b) in tags:
+        L, NT = w.L[s], w.n_replicas[s]
+        Hr = orc.energy(L, np.asarray(Js[s], np.float64), eng.get_spins(s, c, b))
+        assert abs(H[off[s] + c * NT + b] - Hr) <= 2e-5 * abs(Hr)
     eng.close()
