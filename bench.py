@@ -52,6 +52,7 @@ def parse():
     p.add_argument("--policy", default="auto", choices=["auto", "streaming", "resident"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-autotune", action="store_true")
+    p.add_argument("--log", default="", help="also append the line as a JSON-lines run record to this file")
     p.add_argument("--no-cpu", action="store_true")
     return p.parse_args()
 
@@ -284,6 +285,9 @@ def reference_arm(args):
         "e2e": {"value": v, "unit": "updates/ns", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+    if args.log:
+        from paper_1006_4247_gb300 import runlog
+        runlog.record(args.log, "bench_reference", line["config"], {k: v for k, v in line.items() if k != "config"})
 
 
 # ---------------------------------------------------------------------------
@@ -501,6 +505,10 @@ def ours(args):
             "kernel_share": share, "kernel_ms_profiled": prof_ms, "kernel_launches_profiled": prof_launches,
         }
         print(json.dumps(line), flush=True)
+        if args.log:
+            from paper_1006_4247_gb300 import runlog
+            runlog.record(args.log, "bench", line["config"], {k: v for k, v in line.items() if k != "config"},
+                          engine=runlog.engine_summary(eng))
     eng.close()
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -323,6 +323,8 @@ class Engine:
         opt.start = PT_START_ORDERED if start in ("ordered", PT_START_ORDERED) else PT_START_RANDOM
         st = _torch_stream() if stream is None else stream
         opt.stream = st
+        self.precision = "fp64" if opt.precision == PT_FP64 else "fp32"
+        self.seed = int(opt.seed)
         self._alloc = None
         if use_torch_allocator:
             self._alloc = _TorchAllocator()

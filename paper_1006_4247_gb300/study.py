@@ -284,18 +284,26 @@ def main(argv=None):
                     help="replica study: the standard swap at the paper's N_T only")
     ap.add_argument("--equilibration", type=int, default=0, help="runs of the equilibration study (0: off)")
     ap.add_argument("--learned-large", action="store_true", help="learned ladder at L (e.g. 48) vs geometric")
+    ap.add_argument("--log", default="", help="also append the result as a JSON-lines run record to this file")
     a = ap.parse_args(argv)
     nt = a.n_temps or {16: 15, 24: 27, 32: 43}.get(a.L, ladder.default_n_temps(a.L, 1 / T_MAX, 1 / T_MIN))
     if a.learned_large:
-        print(json.dumps(learned_large(a.L, cycles=a.cycles, burn=a.burn)))
+        kind, out = "learned_large", learned_large(a.L, cycles=a.cycles, burn=a.burn)
     elif a.equilibration:
-        print(json.dumps(equilibration(a.L, nt, a.equilibration, a.cycles, a.kappa)))
+        kind, out = "equilibration", equilibration(a.L, nt, a.equilibration, a.cycles, a.kappa)
     elif a.replicas:
         nts = [int(v) for v in a.replicas.split(",")]
-        print(json.dumps(replicas(a.L, nts, nt, a.sets, a.cycles, a.burn, a.kappa,
-                                  plain_all=not a.plain_reference_only)))
+        kind, out = "replicas", replicas(a.L, nts, nt, a.sets, a.cycles, a.burn, a.kappa,
+                                         plain_all=not a.plain_reference_only)
     else:
-        print(json.dumps(protocol(a.L, nt, a.sets, a.cycles, a.burn, a.kappa, methods=tuple(a.methods.split(",")))))
+        kind, out = "protocol", protocol(a.L, nt, a.sets, a.cycles, a.burn, a.kappa,
+                                         methods=tuple(a.methods.split(",")))
+    print(json.dumps(out))
+    if a.log:
+        from . import runlog
+        cfg = {k: v for k, v in vars(a).items() if k != "log"}
+        cfg["n_temps"] = nt
+        runlog.record(a.log, "study_" + kind, cfg, out)
 
 
 if __name__ == "__main__":
