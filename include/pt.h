@@ -309,6 +309,15 @@ pt_status pt_autotune(pt_handle h, int n_hb, int n_or, int *choice, double *best
  * until pt_autotune decides. */
 pt_status pt_get_paths(pt_handle h, int *choice, int *ctas);
 
+/* Set the sweep path of every sample from codes in the encoding of
+ * pt_get_paths (host int [n_samples]), e.g. the choices of an earlier
+ * pt_autotune of the same batch shape kept in a cache, under
+ * PT_POLICY_AUTO.  Nothing changes if a code is not a path of its sample:
+ * PT_ERR_ARG for a malformed code or a vector width the row length does not
+ * allow, PT_ERR_STATE for a resident shape the sample does not fit.  The
+ * chain is unchanged (every path runs the same updates). */
+pt_status pt_set_paths(pt_handle h, const int *choice);
+
 /* Release all device memory of the handle.  NULL is accepted. */
 pt_status pt_destroy(pt_handle h);
 

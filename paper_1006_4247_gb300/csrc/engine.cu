@@ -1297,6 +1297,31 @@ pt_status pt_get_paths(pt_handle e, int* choice, int* ctas) {
     return PT_OK;
 }
 
+pt_status pt_set_paths(pt_handle e, const int* choice) {
+    if (!e || !choice) return fail(PT_ERR_ARG, "NULL argument");
+    for (int s = 0; s < e->S; ++s) {
+        const SampleDesc& sd = e->samples[s];
+        const int res = choice[s] / 10, vec = choice[s] % 10;
+        if (choice[s] < 0 || res > 2 || (vec != 1 && vec != 2 && vec != 4) || sd.hL % vec || (e->fp64 && vec == 4))
+            return fail(PT_ERR_ARG, "sample %d: path code %d is not a path of this sample", s, choice[s]);
+        if (res == 1 && resident_cluster(sd, e->fp64, vec) == 0)
+            return fail(PT_ERR_STATE, "sample %d: no resident kernel with %d sites per thread", s, vec);
+        if (res == 2 && resident_cluster_narrow(sd, e->fp64, vec) == 0)
+            return fail(PT_ERR_STATE, "sample %d: no narrow cluster with %d sites per thread", s, vec);
+    }
+    pt_status st = sync(e);
+    if (st != PT_OK) return st;
+    e->tuned_vec.assign(e->S, 0);
+    e->tuned_res.assign(e->S, -1);
+    for (int s = 0; s < e->S; ++s) {
+        e->tuned_vec[s] = choice[s] % 10;
+        e->tuned_res[s] = choice[s] / 10;
+    }
+    e->policy = PT_POLICY_AUTO;
+    choose_paths(e);
+    return rebuild_lists(e);
+}
+
 pt_status pt_destroy(pt_handle e) {
     if (!e) return PT_OK;
     e->release();

@@ -12,6 +12,7 @@ and may own the device memory through the allocator callback
 from __future__ import annotations
 
 import ctypes as C
+import json
 import os
 import threading
 
@@ -33,7 +34,7 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 # Entry points declared in include/pt.h (the symbol test checks this list
 # against the header).
 ENTRY_POINTS = ["pt_options_default", "pt_create", "pt_create_batch", "pt_sweep", "pt_sweep_samples",
-                "pt_cycles", "pt_autotune", "pt_get_paths", "pt_exchange",
+                "pt_cycles", "pt_autotune", "pt_get_paths", "pt_set_paths", "pt_exchange",
                 "pt_measure", "pt_measure_device", "pt_get_stats", "pt_get_spins", "pt_set_spins",
                 "pt_set_params", "pt_set_rng_step", "pt_get_rng_step", "pt_save", "pt_load",
                 "pt_profile", "pt_profile_read", "pt_set_policy", "pt_set_wait_limit", "pt_energy_noalloc",
@@ -84,6 +85,7 @@ def load_library(path: str = LIB_PATH):
                 "pt_cycles": (ip, [vp, ip, ip, ip, C.POINTER(C.c_int), ip, ip]),
                 "pt_autotune": (ip, [vp, ip, ip, C.POINTER(C.c_int), dp]),
                 "pt_get_paths": (ip, [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+                "pt_set_paths": (ip, [vp, C.POINTER(C.c_int)]),
                 "pt_exchange": (ip, [vp, ip, fp]),
                 "pt_measure": (ip, [vp, dp, dp, dp]),
                 "pt_measure_device": (ip, [vp, vp, vp, vp]),
@@ -187,6 +189,18 @@ def pt_autotune(h, n_hb, n_or, n_samples):
     best = np.zeros(n_samples)
     _check(load_library().pt_autotune(h, int(n_hb), int(n_or), _ptr(choice, C.c_int), _ptr(best, C.c_double)))
     return choice, best
+
+
+def pt_set_paths(h, choice):
+    c = np.ascontiguousarray(choice, np.int32)
+    _check(load_library().pt_set_paths(h, _ptr(c, C.c_int)))
+
+
+def autotune_cache_key(L, NT, copies, precision, n_hb, n_or, device_name):
+    """Key of an autotuner result: the batch shape, precision, block and GPU."""
+    return json.dumps({"L": [int(v) for v in L], "NT": [int(v) for v in NT], "copies": int(copies),
+                       "precision": precision, "n_hb": int(n_hb), "n_or": int(n_or), "gpu": device_name},
+                      sort_keys=True)
 
 
 def pt_exchange(h, mode, eps=None):
@@ -375,8 +389,40 @@ class Engine:
         _check(load_library().pt_get_paths(self.h, ch, ct))
         return np.array(ch[:], np.int32), np.array(ct[:], np.int32)
 
-    def autotune(self, n_hb=1, n_or=1):
-        return pt_autotune(self.h, n_hb, n_or, self.S)
+    def autotune(self, n_hb=1, n_or=1, cache=None):
+        """Time the candidate paths (pt_autotune) and return (choice, best_ms).
+        With `cache` (a JSON file), a result stored there for the same batch
+        shape, precision, block and GPU is applied with pt_set_paths instead
+        of timing again, and a new result is stored."""
+        key = None
+        if cache:
+            import torch
+            key = autotune_cache_key(self.L, self.NT, self.C, self.precision, n_hb, n_or,
+                                     torch.cuda.get_device_name())
+            table = {}
+            if os.path.exists(cache):
+                with open(cache) as fh:
+                    table = json.load(fh)
+            if key in table:
+                choice = np.array(table[key]["choice"], np.int32)
+                self.set_paths(choice)
+                return choice, np.array(table[key]["best_ms"])
+        choice, best = pt_autotune(self.h, n_hb, n_or, self.S)
+        if cache:
+            table = {}
+            if os.path.exists(cache):
+                with open(cache) as fh:
+                    table = json.load(fh)
+            table[key] = {"choice": choice.tolist(), "best_ms": best.tolist()}
+            tmp = cache + ".tmp"
+            with open(tmp, "w") as fh:
+                json.dump(table, fh, indent=1)
+            os.replace(tmp, cache)
+        return choice, best
+
+    def set_paths(self, choice):
+        """Apply per-sample path codes (the encoding of pt_get_paths)."""
+        pt_set_paths(self.h, choice)
 
     def energies(self):
         out = np.zeros(self.R)

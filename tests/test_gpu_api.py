@@ -172,3 +172,31 @@ def test_bounded_wait_gives_up_and_handle_stays_usable(monkeypatch):
         plain.set_wait_limit(16, inject=True)  # no bulk-copy kernel to fault
     assert ei.value.status == pt.PT_ERR_STATE
     plain.close()
+
+
+def test_set_paths_and_cached_autotune(tmp_path):
+    """pt_set_paths applies path codes (and refuses codes a sample cannot
+    run, changing nothing); the autotuner's result is stored in a cache file
+    and applied from it the next time, without timing again."""
+    eng, J, B = make_engine(32, 2, 3, 2, "fp32", seed=3)
+    eng.set_paths([24, 24])
+    choice, ctas = eng.paths()
+    assert list(choice) == [24, 24] and list(ctas) == [8, 8]
+    eng.set_paths([14, 4])
+    choice, ctas = eng.paths()
+    assert list(choice) == [14, 4] and list(ctas) == [4, 0]
+    for bad, status in (([3, 4], pt.PT_ERR_ARG), ([34, 4], pt.PT_ERR_ARG), ([11, 4], pt.PT_ERR_STATE)):
+        with pytest.raises(pt.PtError) as ei:
+            eng.set_paths(bad)
+        assert ei.value.status == status
+        assert list(eng.paths()[0]) == [14, 4]
+    f = str(tmp_path / "tune.json")
+    c1, b1 = eng.autotune(1, 2, cache=f)
+    assert os.path.exists(f)
+    eng.set_paths([4, 4])
+    c2, b2 = eng.autotune(1, 2, cache=f)  # from the file
+    assert (c2 == c1).all() and (b2 == b1).all()
+    assert (eng.paths()[0] == c1).all()
+    eng.sweep(1, 1)
+    assert np.isfinite(eng.energies()).all()
+    eng.close()

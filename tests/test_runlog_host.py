@@ -33,3 +33,14 @@ def test_records_append_and_read_back(tmp_path):
     got = runlog.read(f, kind="bench")
     assert len(got) == 1 and got[0]["results"]["value"] == 1.5 and got[0]["engine"]["seed"] == 17
     assert got[0]["time"].endswith("Z")
+
+
+def test_autotune_cache_key_names_everything_the_choice_depends_on():
+    from paper_1006_4247_gb300 import pt
+    k = pt.autotune_cache_key([16, 32], [24, 48], 2, "fp32", 1, 40, "GB300")
+    assert k == pt.autotune_cache_key((16, 32), np.array([24, 48]), 2, "fp32", 1, 40, "GB300")
+    for other in (pt.autotune_cache_key([16, 32], [24, 48], 2, "fp64", 1, 40, "GB300"),
+                  pt.autotune_cache_key([16, 32], [24, 48], 2, "fp32", 1, 20, "GB300"),
+                  pt.autotune_cache_key([16, 32], [24, 48], 2, "fp32", 1, 40, "B200"),
+                  pt.autotune_cache_key([32, 16], [48, 24], 2, "fp32", 1, 40, "GB300")):
+        assert other != k
