@@ -12,7 +12,7 @@ Long run (paired: the float and double engines share couplings, initial
 spins and Philox streams; per chain the difference of time averages, mean and
 standard error over the 32 chains): energy per site at every beta, the
 acceptance of every pair, chi at every beta.  The numbers are printed (run
-with -s) and recorded in DESIGN.md.
+with -s).
 """
 import json
 import os
