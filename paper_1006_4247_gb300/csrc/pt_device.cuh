@@ -153,9 +153,19 @@ template <typename T> struct V3 { T x, y, z; };
 template <typename T>
 __device__ __forceinline__ T dot(const V3<T>& a, const V3<T>& b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
 
+// s <- s / |s|.  Every caller rotates, reflects or builds a unit vector, so
+// |s|^2 = 1 + d with d a few rounding errors.  In double the factor is then
+// taken from the first Newton step for x^(-1/2) at x = 1, 1 - d/2, whose
+// error 3d^2/8 is below the rounding of the result for |d| < 1e-8: two
+// instructions instead of a square root and a division on GB300's slow FP64
+// pipe; larger |d| (never seen) take the exact factor.  Float uses the
+// hardware reciprocal square root.
 template <typename T>
 __device__ __forceinline__ void renorm(V3<T>& s) {
-    T inv = M<T>::rsqrt_(dot(s, s));
+    const T ss = dot(s, s);
+    T inv;
+    if (sizeof(T) == 8 && fabs(ss - (T)1) < (T)1e-8) inv = (T)1.5 - (T)0.5 * ss;
+    else inv = M<T>::rsqrt_(ss);
     s.x *= inv; s.y *= inv; s.z *= inv;
 }
 
