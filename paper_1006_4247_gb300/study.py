@@ -149,7 +149,7 @@ def replicas(L, n_temps_list, reference_nt, n_sets=10, cycles=20000, burn=5000, 
     arms = ("plain", "decimation", "coolheat", "coolheat_learned")
     out = {"L": L, "reference_nt": reference_nt, "n_sets": n_sets, "cycles": cycles, "burn": burn,
            "sweeps_per_cycle": spc, "t_R": {a: {} for a in arms}, "acc_min": {a: {} for a in arms},
-           "t_R_se": {a: {} for a in arms}}
+           "t_R_se": {a: {} for a in arms}, "tau_int_median": {a: {} for a in arms}}
     try:
         for nt in sorted(set(list(n_temps_list) + [reference_nt])):
             b = paper_ladder(nt)
@@ -166,8 +166,10 @@ def replicas(L, n_temps_list, reference_nt, n_sets=10, cycles=20000, burn=5000, 
                     prop = net.propose_many([(L, j, 1 / T_MAX, 1 / T_MIN) for j in J], n_temps=nt)
                     betas = np.stack([p[0] for p in prop])
                     eps = np.stack([p[1] for p in prop])
-                acc, rt, _ = run_method(L, J, betas, mode, eps, cycles, burn, seed=13)
+                acc, rt, chi = run_method(L, J, betas, mode, eps, cycles, burn, seed=13)
                 tR = cycles * spc / np.maximum(rt, 1)
+                # sweeps to decorrelate chi at the lowest temperature (c = 4), median over the sets
+                out["tau_int_median"][arm][nt] = float(np.median([tau_int(chi[:, k]) * spc for k in range(n_sets)]))
                 out["t_R"][arm][nt] = float(tR.mean())
                 out["t_R_se"][arm][nt] = float(tR.std(ddof=1) / math.sqrt(n_sets))
                 out["acc_min"][arm][nt] = float(acc.min(1).mean())
