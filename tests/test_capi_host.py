@@ -88,3 +88,25 @@ def test_python_binding_fails_loudly_without_library(tmp_path):
         mod._lib = None
         mod.load_library(str(tmp_path / "missing.so"))
     importlib.reload(pt)
+
+
+def test_handle_calls_reject_null_on_the_host(lib):
+    """Every call that takes a handle returns PT_ERR_ARG for a NULL handle
+    (or NULL output) without touching a device."""
+    from paper_1006_4247_gb300 import pt
+    i = C.c_int(0)
+    codes = (C.c_int * 2)(14, 4)
+    u = C.c_uint64(0)
+    assert lib.pt_sweep_samples(None, 1, codes) == pt.PT_ERR_ARG
+    assert lib.pt_cycles(None, 1, 1, 1, None, 0, 0) == pt.PT_ERR_ARG
+    assert lib.pt_exchange(None, 0, None) == pt.PT_ERR_ARG
+    assert lib.pt_measure(None, None, None, None) == pt.PT_ERR_ARG
+    assert lib.pt_get_paths(None, codes, None) == pt.PT_ERR_ARG
+    assert lib.pt_set_paths(None, codes) == pt.PT_ERR_ARG
+    assert lib.pt_set_wait_limit(None, 16, 1) == pt.PT_ERR_ARG
+    assert lib.pt_set_policy(None, 0) == pt.PT_ERR_ARG
+    assert lib.pt_get_rng_step(None, C.byref(u)) == pt.PT_ERR_ARG
+    assert lib.pt_profile(None, 1) == pt.PT_ERR_ARG
+    assert lib.pt_save(None, b"x") == pt.PT_ERR_ARG
+    assert lib.pt_mlp_destroy(None) in (pt.PT_OK, pt.PT_ERR_ARG)
+    assert "NULL" in lib.pt_last_error().decode()
