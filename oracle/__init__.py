@@ -102,6 +102,7 @@ def _load():
                                                   C.c_double, _dp, _dp,
                                                   C.POINTER(C.c_double),
                                                   C.POINTER(C.c_double)]),
+                "orc_test_set_jacobian_variant": (None, [C.c_int]),
                 "orc_exchange_coolheat": (None, [C.c_int, _dp, C.c_int, _dp, _dp, _dp,
                                                  _dp, _i32p, _i32p, _i64p, _i64p,
                                                  _i64p, _u64, _u32, _u32, _u64]),
@@ -297,6 +298,25 @@ def coolheat_lnA(L, J, s1, s2, H1, H2, b1, b2, eps):
                                    float(H1), float(H2), float(b1), float(b2),
                                    float(eps), t1, t2, C.byref(Hc), C.byref(Hh))
     return lnA, t1.reshape(N, 3), t2.reshape(N, 3), Hc.value, Hh.value
+
+
+class jacobian_variant:
+    """Test hook (context manager): run the cooling/heating acceptance with
+    the Jacobian of the heated configuration taken at its pre-image (0, the
+    default and the only correct choice), at the heated configuration itself
+    (1, the printed formula read literally) or left out (2), so that a test
+    can show that the exactness check detects the wrong choices."""
+
+    def __init__(self, v):
+        self.v = int(v)
+
+    def __enter__(self):
+        _load().orc_test_set_jacobian_variant(self.v)
+        return self
+
+    def __exit__(self, *exc):
+        _load().orc_test_set_jacobian_variant(0)
+        return False
 
 
 # --------------------------------------------------------------------------

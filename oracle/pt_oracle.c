@@ -534,6 +534,17 @@ double orc_heat_sweep(int L, const double *J, double *s, double eps)
     return lnJ;
 }
 
+/* Test hook, not a reading of the paper: where the acceptance ratio takes
+ * the Jacobian of the heated configuration.  0 (the default, used by
+ * everything but the power test of the exactness check): ln det J_C at the
+ * pre-image C^-1(s2), as the involution requires.  1: at s2 itself, the
+ * paper's printed formula read literally.  2: no Jacobian terms at all.
+ * Variants 1 and 2 break detailed balance; the test suite shows that its
+ * exactness check detects them. */
+static int orc_jacobian_variant = 0;
+
+void orc_test_set_jacobian_variant(int v) { orc_jacobian_variant = v; }
+
 /* Cooling/heating exchange of the pair (beta_1 < beta_2): the configuration
  * at beta_1 is cooled and proposed at beta_2, the one at beta_2 is heated
  * and proposed at beta_1.  The map is an involution, so
@@ -549,6 +560,16 @@ double orc_coolheat_lnA(int L, const double *J, const double *s1,
     memcpy(t2, s2, sizeof(double) * 3 * N);
     double lnJ1 = orc_cool_sweep(L, J, t1, eps);
     double lnJ2 = orc_heat_sweep(L, J, t2, eps);
+    if (orc_jacobian_variant == 1) {
+        /* ln det J_C at s2: cool a copy of s2 and keep only its Jacobian */
+        double *tmp = (double *)malloc(sizeof(double) * 3 * N);
+        memcpy(tmp, s2, sizeof(double) * 3 * N);
+        lnJ2 = orc_cool_sweep(L, J, tmp, eps);
+        free(tmp);
+    } else if (orc_jacobian_variant == 2) {
+        lnJ1 = 0.0;
+        lnJ2 = 0.0;
+    }
     *Hc = orc_energy(L, J, t1);
     *Hh = orc_energy(L, J, t2);
     return -b2 * (*Hc) - b1 * (*Hh) + b1 * H1 + b2 * H2 + lnJ1 - lnJ2;

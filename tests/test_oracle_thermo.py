@@ -35,98 +35,106 @@ def test_beta_zero_closed_forms(orc):
     assert abs(chi.mean() - 1.0) < 5 * chi.std() / np.sqrt(chi.size)
 
 
-def _cycles_L(L):
-    """Closed loops of bonds at the lowest orders: plaquettes, and for L <= 4
-    the loops that wind around the periodic lattice.  Each loop is a list of
-    (mu, x) bonds."""
+def _lattice_graph(L):
+    """The periodic L^3 lattice as a graph: {(x, y): [(mu, x'), ...]} with
+    x < y, listing the bonds (mu, x') that join the two sites (two of them
+    for every neighbour pair at L = 2, where they act as one bond of coupling
+    J_eff = their sum; one otherwise)."""
     N = L ** 3
 
-    def idx(i, j, k):
-        return (i % L) + L * ((j % L) + L * (k % L))
-
     def step(x, mu):
-        i, j, k = x % L, (x // L) % L, x // (L * L)
-        d = [0, 0, 0]
-        d[mu] = 1
-        return idx(i + d[0], j + d[1], k + d[2])
+        c = [x % L, (x // L) % L, x // (L * L)]
+        c[mu] = (c[mu] + 1) % L
+        return c[0] + L * (c[1] + L * c[2])
 
-    loops = []
+    g = {}
     for x in range(N):
         for mu in range(3):
-            for nu in range(mu + 1, 3):
-                xm = step(x, mu)
-                xn = step(x, nu)
-                loops.append([(mu, x), (nu, xm), (mu, xn), (nu, x)])
-    if L in (3, 4):
-        for mu in range(3):
-            for x in range(N):
-                i, j, k = x % L, (x // L) % L, x // (L * L)
-                if (i, j, k)[mu] != 0:
-                    continue
-                line, y = [], x
-                for _ in range(L):
-                    line.append((mu, y))
-                    y = step(y, mu)
-                loops.append(line)
-    return loops
+            y = step(x, mu)
+            g.setdefault((min(x, y), max(x, y)), []).append((mu, x))
+    return g
+
+
+def _simple_cycles(L, max_len=6):
+    """Every simple cycle (closed walk through distinct sites) of at most
+    max_len edges of the lattice graph, once each, as a list of edge keys."""
+    g = _lattice_graph(L)
+    adj = {}
+    for (x, y) in g:
+        adj.setdefault(x, []).append(y)
+        adj.setdefault(y, []).append(x)
+    out = []
+    for v in sorted(adj):
+        stack = [(v, [v])]
+        while stack:
+            x, path = stack.pop()
+            for y in adj[x]:
+                if y == v and len(path) >= 3 and path[1] < path[-1]:
+                    cyc = path + [v]
+                    out.append([(min(a, b), max(a, b)) for a, b in zip(cyc[:-1], cyc[1:])])
+                elif y > v and y not in path and len(path) < max_len:
+                    stack.append((y, path + [y]))
+    return out
+
+
+def _series_parts(L, J, beta):
+    """ln Z of the high-temperature expansion, through the graphs of six
+    bonds (each bond weight e^{u s.s'} expanded in Legendre polynomials,
+    u = beta J, with the single-bond factors ln(sinh u / u) kept exactly):
+    every simple cycle C contributes 3 prod_{b in C} t(u_b), t = Langevin
+    function (the vertex integrals of the l = 1 terms around the loop).  On
+    the L = 3 lattice the winding cycles have three bonds, which brings two
+    more terms of order u^6 on each of them: the loop of l = 2 terms,
+    5 prod a2(u_b) with a2 = 1 - 3 t(u)/u, and the cumulant -(3 prod t)^2 / 2
+    (a loop cannot be occupied twice).  Loops that share only a site
+    contribute the product of their weights to Z, so they cancel in ln Z.
+    Returns (single-bond part, cycles of fewer than six bonds, the six-bond
+    order) as functions of beta."""
+    g = _lattice_graph(L)
+    Je = {k: sum(J[mu, x] for mu, x in bonds) for k, bonds in g.items()}
+    cycles = _simple_cycles(L, 6)
+
+    def t_of(b, k):
+        return langevin(np.array([b * Je[k]]))[0]
+
+    def a2_of(b, k):
+        u = b * Je[k]
+        return u * u / 15.0 if abs(u) < 1e-3 else 1.0 - 3.0 * langevin(np.array([u]))[0] / u
+
+    def low(b):
+        return sum(3 * np.prod([t_of(b, k) for k in c]) for c in cycles if len(c) < 6)
+
+    def six(b):
+        v = sum(3 * np.prod([t_of(b, k) for k in c]) for c in cycles if len(c) == 6)
+        if L == 3:
+            for c in (c for c in cycles if len(c) == 3):
+                w = 3 * np.prod([t_of(b, k) for k in c])
+                v += 5 * np.prod([a2_of(b, k) for k in c]) - 0.5 * w * w
+        return v
+
+    Jv = np.array(list(Je.values()))
+    return (lambda b: -(Jv * langevin(b * Jv)).sum()), low, six
+
+
+def _ddb(f, b, h=1e-5):
+    return (f(b + h) - f(b - h)) / (2 * h)
 
 
 def _highT_energy(L, J, beta):
-    """<H> from ln Z = sum_b ln(sinh u_b/u_b) + 3 sum_loops prod_b t(u_b),
-    t = Langevin function, u = beta J (expansion in Legendre polynomials of
-    each bond weight; the lowest neglected graphs enter <H> at O(beta^5))."""
-    loops = _cycles_L(L)
-
-    def loop_part(b):
-        t = langevin(b * J)
-        return 3 * sum(np.prod([t[mu, x] for mu, x in lp]) for lp in loops)
-
-    h = 1e-5
-    d = (loop_part(beta + h) - loop_part(beta - h)) / (2 * h)
-    return -(J * langevin(beta * J)).sum() - d
+    """<H> = -d ln Z / d beta of the series through six-bond graphs."""
+    single, low, six = _series_parts(L, J, beta)
+    return single(beta) - _ddb(low, beta) - _ddb(six, beta)
 
 
-def _highT_energy_L2(J, beta):
-    """L = 2: the two bonds of each neighbour pair merge into J_eff; the graph
-    is the 3-cube (12 edges, 6 faces)."""
-    L = 2
-
-    def idx(i, j, k):
-        return (i % 2) + 2 * ((j % 2) + 2 * (k % 2))
-
-    edges = {}
-    for x in range(8):
-        i, j, k = x % 2, (x // 2) % 2, x // 4
-        for mu in range(3):
-            d = [0, 0, 0]
-            d[mu] = 1
-            y = idx(i + d[0], j + d[1], k + d[2])
-            key = (min(x, y), max(x, y))
-            edges[key] = edges.get(key, 0.0) + J[mu, x]
-    faces = []
-    for mu in range(3):
-        for nu in range(mu + 1, 3):
-            for base in range(8):
-                bi = [base % 2, (base // 2) % 2, base // 4]
-                if bi[mu] or bi[nu]:
-                    continue
-                corners = []
-                for a, b in ((0, 0), (1, 0), (1, 1), (0, 1)):
-                    c = list(bi)
-                    c[mu] += a
-                    c[nu] += b
-                    corners.append(idx(*c))
-                faces.append([(min(corners[n], corners[(n + 1) % 4]),
-                               max(corners[n], corners[(n + 1) % 4])) for n in range(4)])
-    assert len(edges) == 12 and len(faces) == 6
-    Je = np.array(list(edges.values()))
-
-    def loop_part(b):
-        return 3 * sum(np.prod([langevin(np.array([b * edges[e]]))[0] for e in f]) for f in faces)
-
-    h = 1e-5
-    d = (loop_part(beta + h) - loop_part(beta - h)) / (2 * h)
-    return -(Je * langevin(beta * Je)).sum() - d
+def _highT_remainder(L, J, beta):
+    """Allowance for the graphs left out: the size of the six-bond order's
+    contribution to <H>.  The first omitted orders are eight-bond graphs
+    (L = 2, 4; smaller than the six-bond order by about (beta J / 3)^2 times
+    the ratio of their counts, 0.1 at beta = 0.3) and seven-bond cycles
+    (L = 3; about beta |J| / 3 times the lattice's growth constant of cycles,
+    below 0.5 at beta = 0.3), so the six-bond order bounds them with margin."""
+    _, _, six = _series_parts(L, J, beta)
+    return abs(_ddb(six, beta))
 
 
 @pytest.mark.parametrize("L,order", [(2, 0), (4, 0), (3, 1)])
@@ -138,8 +146,8 @@ def test_high_temperature_series(orc, L, order):
     Hs, _, _ = run.cycles(n, n_hb=1, n_or=1, mode=0, order=order)
     m, e = block_mean_err(Hs[n // 10:].reshape(-1, 2 * 3).reshape(-1, 2, 3).mean(1))
     for b, beta in enumerate(betas):
-        ref = _highT_energy_L2(J, beta) if L == 2 else _highT_energy(L, J, beta)
-        assert abs(m[b] - ref) < 4.5 * e[b] + 1e-3, (L, beta, m[b], ref, e[b])
+        ref = _highT_energy(L, J, beta)
+        assert abs(m[b] - ref) < 4.5 * e[b] + _highT_remainder(L, J, beta), (L, beta, m[b], ref, e[b])
 
 
 def test_modified_exchanges_sample_the_same_ensemble(orc):
@@ -177,3 +185,33 @@ def test_modified_exchanges_raise_acceptance(orc):
         acc[mode] = run.acc.sum(0) / run.prop.sum(0)
     assert (acc[1] > acc[0]).all() and acc[1].mean() > 1.5 * acc[0].mean()
     assert acc[2].mean() > 1.2 * acc[0].mean()
+
+
+def test_exactness_check_detects_wrong_jacobians(orc):
+    """Power of the exactness check above (same lattice, couplings, ladder,
+    cooling parameter and run length).  The cooling/heating acceptance is run
+    with the Jacobian of the heated configuration taken where section III.B's
+    printed formula, read literally, puts it (at s2 itself instead of at its
+    pre-image C^-1 s2), and with no Jacobian at all.  Both break detailed
+    balance; the check must see each of them: <H>(beta) at some temperature
+    more than 6 combined standard errors from the standard swap's (the check
+    passes the correct placement at 4.5)."""
+    L = 2
+    J = W.couplings(L, 90).astype(np.float64)
+    betas = np.array([0.8, 1.3, 1.9, 2.6])
+    n = 30000
+
+    def mean_H(mode, variant):
+        with orc.jacobian_variant(variant):
+            run = orc.Run(L, J, betas, n_copies=2, seed=100 + mode, eps=0.06)
+            Hs, _, _ = run.cycles(n, n_hb=1, n_or=1, mode=mode)
+        return block_mean_err(Hs[n // 10:].mean(1))
+
+    m0, e0 = mean_H(0, 0)
+    for variant in (1, 2):
+        m, e = mean_H(2, variant)
+        z = np.abs(m - m0) / np.sqrt(e ** 2 + e0 ** 2)
+        assert z.max() > 6.0, (variant, z)
+    # the hook is reset on leaving the context: the correct placement again
+    m, e = mean_H(2, 0)
+    assert within(m, e, m0, e0, 4.5).all()
