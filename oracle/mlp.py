@@ -7,7 +7,7 @@ kernels.
 The network and its decoding are this project's design (the paper has no
 network); the decoding serves the paper's tempering parameters: the ladder of
 inverse temperatures beta_i and the cooling/heating parameter epsilon of every
-pair (Sec. 2.3, whose optimal value depends on the pair and falls with
+pair (section III.B, whose optimal value depends on the pair and falls with
 beta_{i+1}/beta_i).  Everything is written out as its definition, in double
 precision, one operation at a time:
 

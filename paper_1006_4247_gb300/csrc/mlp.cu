@@ -1,7 +1,7 @@
 // mlp.cu -- the learned ladder: a 4 -> 64 -> 64 -> 2P+1 perceptron that maps a
 // sample's description (ln L, beta_min, beta_max, coupling statistic) to the
 // shape of its inverse-temperature ladder, the cooling/heating parameter
-// along it (Sec. 2.3: the optimal epsilon depends on the pair of
+// along it (section III.B: the optimal epsilon depends on the pair of
 // temperatures and falls with beta_{i+1}/beta_i) and the total rejection
 // length of the range, which fixes the number of replicas.  It only chooses
 // parameters of the tempering; the Markov chain is exact for any ladder.

@@ -1,7 +1,7 @@
 """Learned inverse-temperature ladder and per-pair cooling/heating parameter.
 
-The paper tempers with a geometric ladder of temperatures (Sec. 4) and one
-cooling/heating parameter epsilon for all pairs (Sec. 2.3), which it notes
+The paper tempers with a geometric ladder of temperatures (section IV) and one
+cooling/heating parameter epsilon for all pairs (section III.B), which it notes
 should depend on the pair and fall with beta_{i+1}/beta_i.  This module
 replaces both choices by the proposals of a small network (``pt.Mlp``, the
 pt_mlp_* kernels), trained on data the engine itself produces:
@@ -42,7 +42,7 @@ KAPPA_GRID = (0.04, 0.07, 0.1, 0.13, 0.17, 0.22)
 DATA_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data")
 TRAIN_FILE = os.path.join(DATA_DIR, "ladder_train.npz")
 WEIGHTS_FILE = os.path.join(DATA_DIR, "ladder_net.npz")
-PAPER_WINDOW = (1 / 0.19, 1 / 0.12)  # Sec. 4: T from 0.12 to 0.19
+PAPER_WINDOW = (1 / 0.19, 1 / 0.12)  # section IV: T from 0.12 to 0.19
 TRAIN_L = (4, 6, 8, 12, 16, 24, 32)
 TRAIN_WINDOWS = ((2.0, 8.0), (2.5, 8.0), PAPER_WINDOW, (3.0, 6.0), (4.0, 10.0), (1.5, 5.0))
 EPS_SAFETY = 0.9  # eps * max_x sum_6 |J| must stay below 1 (invertible cooling step)
@@ -77,7 +77,7 @@ def eps_bound(L: int, J: np.ndarray) -> float:
 
 
 def geometric(beta_min: float, beta_max: float, n_temps: int) -> np.ndarray:
-    """Geometric ladder (Sec. 4): equal ratios beta_{i+1}/beta_i."""
+    """Geometric ladder (section IV): equal ratios beta_{i+1}/beta_i."""
     return beta_min * (beta_max / beta_min) ** (np.arange(n_temps) / (n_temps - 1))
 
 
@@ -90,7 +90,7 @@ def eps_from_kappa(betas: np.ndarray, kappa, bound: float) -> np.ndarray:
 def default_n_temps(L: int, beta_min: float, beta_max: float) -> int:
     """Replica count of the geometric reference ladder: N_T - 1 proportional
     to L^{3/2} ln(beta_max/beta_min), the constant fixed by the paper's
-    ladders (Sec. 4: T in [0.12, 0.19] with N_T = 15 at L = 16 and 27 at
+    ladders (section IV: T in [0.12, 0.19] with N_T = 15 at L = 16 and 27 at
     L = 24)."""
     return max(3, 1 + int(round(0.48 * L ** 1.5 * math.log(beta_max / beta_min))))
 
@@ -206,7 +206,7 @@ def feedback_kappa(cases, n_iter=10, block=300, kappa0=0.07, delta=0.35, step0=0
                    seed=0, mode="coolheat", n_copies=2, kappa_min=0.005):
     """Per-pair cooling parameter by feedback on the measured acceptance, with
     neither the network nor a scan (the paper notes that epsilon should
-    depend on the pair, Sec. 2.3 and Sec. 4).  Each case is (L, J, betas).
+    depend on the pair, sections III.B and IV.A).  Each case is (L, J, betas).
 
     kappa_i = eps_i / ln(beta_{i+1}/beta_i) is tuned on a log scale.  The
     chain is exact for every epsilon and the proposals of pair i depend on

@@ -1,4 +1,4 @@
-"""The paper's measurement protocol (Sec. 4) on synthetic coupling sets.
+"""The paper's measurement protocol (section IV) on synthetic coupling sets.
 
 For one lattice size: ``n_sets`` Gaussian coupling sets, the geometric ladder
 of the paper (T from 0.12 to 0.19, N_T replicas), two copies per set, update
@@ -7,7 +7,7 @@ run with each exchange method on the same sets.  Reported per method:
 
 * the acceptance of every pair (Table I gives the first and last pair);
 * the round-trip time t_R: sweeps of the run divided by the round trips of
-  all 2 N_T configurations of a set (Sec. 4.2);
+  all 2 N_T configurations of a set (section IV.B);
 * the integrated autocorrelation time of the overlap susceptibility at the
   lowest temperature, tau_int(chi) in sweeps, by automatic windowing (the
   smallest window W with W >= c tau(W), c = 4; Sokal).
@@ -182,7 +182,7 @@ def replicas(L, n_temps_list, reference_nt, n_sets=10, cycles=20000, burn=5000, 
 
 def equilibration(L=16, n_temps=15, n_runs=2000, cycles=1000, kappa=0.1, seed=8500,
                   methods=("plain", "decimation", "coolheat")):
-    """Equilibration from the ordered start (Sec. 4.4, Fig. 1):
+    """Equilibration from the ordered start (section IV.C, Fig. 1):
     n_runs independent runs (independent random numbers) on one coupling set,
     every spin (1, 0, 0) at the start, all runs in one batched engine; the
     mean and standard error over runs of chi at the lowest temperature after

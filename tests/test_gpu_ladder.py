@@ -8,7 +8,7 @@ evaluated on held-out coupling samples at a lattice size it never saw
 
 * the yardstick: the geometric ladder with one cooling/heating parameter for
   all pairs, tuned by a scan on the evaluation samples themselves (the
-  paper's procedure, Sec. 2.3), at the replica count of the paper's rule;
+  paper's procedure, section III.B), at the replica count of the paper's rule;
 * the same geometric ladder with epsilon tuned per pair and per sample from
   that scan (no network: the ablation of the learned parameters);
 * the plain swap on the same geometric ladder (the standard method).

@@ -1,4 +1,4 @@
-"""The paper's protocol (Sec. 4) at L = 16 on ten synthetic coupling sets:
+"""The paper's protocol (section IV) at L = 16 on ten synthetic coupling sets:
 the improved exchanges raise the acceptance and shorten the round-trip time
 as Tables I and II report (decimation ~2.1x, cooling/heating ~2.4-2.6x).
 Trends only: the paper's coupling sets are not available."""

@@ -29,6 +29,6 @@ def test_tau_int_short_or_constant_series():
 def test_paper_ladder():
     b = study.paper_ladder(15)
     assert b[0] == pytest.approx(1 / 0.19) and b[-1] == pytest.approx(1 / 0.12)
-    # equal temperature ratios (Sec. 4)
+    # equal temperature ratios (section IV)
     T = 1 / b
     np.testing.assert_allclose(T[1:] / T[:-1], (0.12 / 0.19) ** (1 / 14))
