@@ -44,7 +44,7 @@ def parse():
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
-    p.add_argument("--workload", default="L16_R24_S64",
+    p.add_argument("--workload", default="L32_R48_S16",
                    choices=["L4_R8_S1", "L16_R24_S64", "L32_R48_S16", "uneven_S256"])
     p.add_argument("--exchange", default=None)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -262,24 +262,29 @@ def reference_arm(args):
     L, NT = w.L[0], w.n_replicas[0]
     J = W.couplings(L, w.j_seed0).astype(np.float64)
     B = W.linear_betas(NT, w.beta_min, w.beta_max)
-    run = oracle.Run(L, J, B, n_copies=w.n_copies, seed=1, eps=w.eps)
     mode = {"plain": 0, "decimation": 1, "coolheat": 2}[w.exchange]
     nor0 = n_or_of(w)[0]
+    # one step = one cycle of one sample; where that is more than about 5 s of
+    # single-thread work (L = 32: 1.3e8 site updates) only its first copy's
+    # chain is run, so that the whole run stays within a few minutes
+    copies = w.n_copies if w.n_copies * NT * L ** 3 * (w.n_hb + nor0) <= 8e7 else 1
+    run = oracle.Run(L, J, B, n_copies=copies, seed=1, eps=w.eps)
     for _ in range(args.warmup):
         run.cycles(1, w.n_hb, nor0, mode, record=False)
-    per_step = w.n_copies * NT * L ** 3 * (w.n_hb + nor0)
+    per_step = copies * NT * L ** 3 * (w.n_hb + nor0)
     t0 = time.perf_counter()
     for _ in range(args.steps):
         run.cycles(1, w.n_hb, nor0, mode, record=True)
     el = time.perf_counter() - t0
     v = per_step * args.steps / (el * 1e9)
-    sample = f"one sample (L={L}, {NT} replicas x {w.n_copies} copies) of {w.name}, one cycle per step"
+    sample = (f"one sample (L={L}, {NT} replicas x {copies} of its {w.n_copies} copies) of {w.name}, "
+              "one cycle per step")
     line = {
         "metric": "site_updates_per_ns", "value": v, "unit": "updates/ns", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "impl": "reference",
-        "config": {"workload": w.name, "L": L, "replicas": NT, "copies": w.n_copies,
+        "config": {"workload": w.name, "L": L, "replicas": NT, "copies": copies,
                    "samples": 1, "n_hb": w.n_hb, "n_or": nor0, "exchange": w.exchange},
         "cpu_baseline": {"value": v, "unit": "updates/ns", "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": "updates/ns", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -354,6 +359,8 @@ def ours(args):
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize()
+    # the shared-memory data path's measured rate: the resident blocks' roofline
+    smem_Bps, smem_bpc, smem_mhz = pt.pt_smem_bandwidth(stream.cuda_stream)
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
@@ -402,28 +409,32 @@ def ours(args):
         83%), so that is the roofline reported.  Per 4-site vector an
         overrelaxation update issues 24 16-byte shared-memory loads (own
         spins 3, neighbour rows 15, couplings 6) and 3 16-byte stores: 108 B
-        per site update, against 152 SMs x 128 B/clock x 2.07 GHz.  The FP32
-        issue view (60 FLOP counted per update) and the streaming-equivalent
-        HBM rate are kept beside it."""
+        per site update, against the rate of a 16-byte shared-memory load
+        stream measured on the device in this run (pt_smem_bandwidth).  The
+        FP32 issue view (60 FLOP counted per update) and the
+        streaming-equivalent HBM rate are kept beside it."""
         upd = sum(w.n_copies * nt * L ** 3 * (w.n_hb + no)
                   for s, (L, nt, no) in enumerate(zip(w.L, w.n_replicas, nor)) if res_flags[s]) * steps
         if pm["resident"] <= 0 or upd == 0:
             return None
         t = pm["resident"] / 1e3
         n_launch = max(ln["resident"], 1)
-        peak_smem = 152 * 128 * 2.07e9
-        peak_alu = 152 * 128 * 2 * 2.07e9
+        peak_smem = smem_Bps
+        n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+        peak_alu = n_sm * 128 * 2 * smem_mhz * 1e6
         traffic = ncu_traffic("k_resident", w.name, args.precision) if uniform else None
         return {"bound": "smem", "achieved": upd * 108.0 / t / 1e12, "peak": peak_smem / 1e12, "unit": "TB/s",
                 "frac": upd * 108.0 / t / peak_smem, "traffic": traffic,
                 "traffic_note": "DRAM bytes per launch (ncu); the replica pool moves once each way per block",
                 "kernel": "k_resident / k_resident_cl (sweep block in shared memory, one CTA or a cluster)",
-                "peak_source": "derived: 152 SMs x 128 B/clock (shared-memory data path) x 2.07 GHz",
+                "peak_source": (f"measured: 16-byte shared-memory load stream on all {n_sm} SMs "
+                                f"(pt_smem_bandwidth): {smem_bpc:.1f} B/clock/SM at {smem_mhz:.0f} MHz"),
                 "alg_bytes_per_launch": upd * 108.0 / n_launch, "avg_launch_us": t / n_launch * 1e6,
                 "effective_hbm_GBps": upd * 36.4 / t / 1e9,
                 "alu": {"achieved": upd * 60.0 / t / 1e12, "peak": peak_alu / 1e12, "unit": "TFLOP/s",
                         "frac": upd * 60.0 / t / peak_alu,
-                        "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz, 60 FLOP per update"}}
+                        "peak_source": (f"derived: {n_sm} SMs x 128 FP32 lanes x 2 FLOP at the probe's "
+                                        f"{smem_mhz:.0f} MHz, 60 FLOP per update")}}
 
     dominant = max(("or", "resident"), key=lambda k: prof_ms.get(k, 0.0))
     share = {k: v / max(sum(prof_ms.values()), 1e-9) for k, v in prof_ms.items()}

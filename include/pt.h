@@ -173,9 +173,27 @@ pt_status pt_measure_device(pt_handle h, double *d_energy, double *d_overlap, do
 pt_status pt_get_stats(pt_handle h, int64_t *proposals, int64_t *accepts,
                        int64_t *round_trips, int32_t *perm);
 
+/* Synchronise and copy, per pair, the terms of the most recent tempering
+ * update's proposal (each pointer may be NULL):
+ *   lnA  double [n_samples][n_copies][n_replicas-1]: the log acceptance ratio
+ *        the Metropolis test used (section I Eq. 1; section III.A Eq. aswap;
+ *        section III.B, ln A = -b2 H[C s1] - b1 H[C^-1 s2] + b1 H[s1]
+ *        + b2 H[s2] + ln det J_C(s1) - ln det J_C(C^-1 s2))
+ *   lnJ  double [n_samples][n_copies][n_replicas-1][2]: for cooling/heating
+ *        ln det J_C(s1) and ln det J_C(C^-1 s2) of that proposal (the
+ *        Jacobian of the cooling sweep at the configuration it cools, and at
+ *        the pre-image of the heated one); 0 for the other exchanges
+ * s1, s2 are the configurations at beta_i and beta_{i+1} when pair i came up.
+ * Uses: the acceptance estimate mean(min(1, e^lnA)) over updates (lower
+ * variance than counting accepted swaps) and tuning of the cooling parameter.
+ * All zero before the first update; not saved by pt_save. */
+pt_status pt_get_exchange_log(pt_handle h, double *lnA, double *lnJ);
+
 /* Copy the configuration at (sample, copy, replica b) to / from the host as
- * double [L^3][3] in natural site order.  pt_set_spins marks the energies for
- * recomputation; spins should be unit vectors. */
+ * double [L^3][3] in natural site order.  pt_set_spins scales every spin
+ * whose squared length differs from 1 by more than 1e-6 to unit length (the
+ * updates' renormalisation only corrects rounding errors; PT_ERR_ARG for a
+ * zero or non-finite spin) and marks the energies for recomputation. */
 pt_status pt_get_spins(pt_handle h, int sample, int copy, int replica, double *xyz);
 pt_status pt_set_spins(pt_handle h, int sample, int copy, int replica, const double *xyz);
 
@@ -277,6 +295,19 @@ pt_status pt_set_wait_limit(pt_handle h, unsigned long long limit, int inject);
 pt_status pt_energy_noalloc(const void *d_spins, int precision, int L, int n_configs,
                             const float *d_couplings, double *d_energy, void *stream);
 
+/* Measured throughput of the shared-memory data path of the current device,
+ * the unit that bounds the resident sweep blocks (a resident replica runs
+ * every half sweep out of shared memory); it is the peak their roofline is
+ * taken against.  Not a step of the method: a probe of the hardware.
+ * Every SM runs two 512-thread CTAs streaming conflict-free 16-byte loads over
+ * 32 KB of shared memory (about 1 ms); the best of three timed launches on
+ * `stream` (cudaStream_t, NULL: legacy stream) is returned, each output may be
+ * NULL: bytes_per_s (all SMs), bytes_per_clock_sm (per SM and SM clock) and
+ * sm_mhz (the SM clock the probe ran at, from clock64 and the global timer).
+ * Synchronises the stream.  Allocates about 160 KB of device memory for the
+ * duration of the call.  Errors: PT_ERR_NOMEM, PT_ERR_CUDA. */
+pt_status pt_smem_bandwidth(void *stream, double *bytes_per_s, double *bytes_per_clock_sm, double *sm_mhz);
+
 /* Enqueue n_cycles update cycles: a block of local updates (n_hb heat-bath
  * sweeps and n_or overrelaxation sweeps, or n_or_samples[s] for sample s when
  * n_or_samples is not NULL), one tempering update with the stored cooling
@@ -326,10 +357,10 @@ pt_status pt_destroy(pt_handle h);
  * bfloat16 weights, float accumulation, float master weights) maps the
  * description of a sample to the parameters of its tempering: the shape of
  * the inverse-temperature ladder, the cooling/heating parameter epsilon of
- * every pair and the number of replicas the range needs.  Sec. 2.3 motivates it (the best epsilon depends on the pair of
- * temperatures and decreases with beta_{i+1}/beta_i; one epsilon for all
- * pairs was the paper's simplification), and Sec. 4 suggests tuning epsilon
- * per pair.  The net only chooses parameters: the chain is exact for every
+ * every pair and the number of replicas the range needs.  Section III.B
+ * motivates it (the best epsilon depends on the pair of temperatures and
+ * decreases with beta_{i+1}/beta_i; one epsilon for all pairs was the paper's
+ * simplification), and section IV.A suggests tuning epsilon per pair.  The net only chooses parameters: the chain is exact for every
  * ladder.  The paper has no network; the design is this library's.
  *
  * Features x (float [4] per row): ln L, beta_min, beta_max, and the coupling

@@ -585,6 +585,8 @@ pt_status create_impl(pt_handle* out, int n_samples, const int* Ls, const int* N
     TRY(upload(e, &d.part, zt));
     TRY(upload(e, &d.Q, zq));
     TRY(upload(e, &d.chi, zx));
+    std::vector<double> zl((size_t)pair * 3, 0.0);
+    TRY(upload(e, &d.xlog, zl));
 #undef TRY
     d.seed = e->seed;
     d.n_samples = e->S;
@@ -1081,6 +1083,23 @@ pt_status pt_get_stats(pt_handle e, int64_t* proposals, int64_t* accepts, int64_
     return sync(e);
 }
 
+pt_status pt_get_exchange_log(pt_handle e, double* lnA, double* lnJ) {
+    if (!e) return fail(PT_ERR_ARG, "NULL handle");
+    if (!lnA && !lnJ) return PT_OK;
+    std::vector<double> tmp((size_t)e->P * 3);
+    CK(cudaMemcpyAsync(tmp.data(), e->d.xlog, sizeof(double) * tmp.size(), cudaMemcpyDeviceToHost, e->stream));
+    const pt_status st = sync(e);
+    if (st != PT_OK) return st;
+    for (int q = 0; q < e->P; ++q) {
+        if (lnA) lnA[q] = tmp[3 * (size_t)q];
+        if (lnJ) {
+            lnJ[2 * (size_t)q] = tmp[3 * (size_t)q + 1];
+            lnJ[2 * (size_t)q + 1] = tmp[3 * (size_t)q + 2];
+        }
+    }
+    return PT_OK;
+}
+
 pt_status pt_get_spins(pt_handle e, int sample, int copy, int replica, double* xyz) {
     if (!e || !xyz) return fail(PT_ERR_ARG, "NULL argument");
     size_t off;
@@ -1106,9 +1125,22 @@ pt_status pt_set_spins(pt_handle e, int sample, int copy, int replica, const dou
     const size_t n = 3ull * L * L * L;
     for (size_t q = 0; q < n; ++q)
         if (!std::isfinite(xyz[q])) return fail(PT_ERR_ARG, "spin component %zu not finite", q);
+    // unit vectors, as every update expects (its renormalisation corrects
+    // rounding errors only): spins already unit to float accuracy are kept
+    // as given, others are scaled to unit length
+    std::vector<double> unit(xyz, xyz + n);
+    for (size_t x = 0; x < n / 3; ++x) {
+        double* v = &unit[3 * x];
+        const double r2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+        if (!(r2 > 0.0)) return fail(PT_ERR_ARG, "spin of site %zu is zero", x);
+        if (std::fabs(r2 - 1.0) > 1e-6) {
+            const double r = std::sqrt(r2);
+            v[0] /= r; v[1] /= r; v[2] /= r;
+        }
+    }
     std::vector<char> tmp(n * e->esz());
-    if (e->fp64) natural_to_split(L, xyz, (double*)tmp.data());
-    else natural_to_split(L, xyz, (float*)tmp.data());
+    if (e->fp64) natural_to_split(L, unit.data(), (double*)tmp.data());
+    else natural_to_split(L, unit.data(), (float*)tmp.data());
     CK(cudaMemcpyAsync((char*)e->d.spins + off * e->esz(), tmp.data(), n * e->esz(), cudaMemcpyHostToDevice, e->stream));
     e->energy_valid = false;
     return sync(e);

@@ -90,7 +90,7 @@ __device__ __forceinline__ bool metropolis(double lnA, double u) { return lnA >=
 template <typename T, int NV>
 __device__ void cluster_sum(cg::cluster_group& cl, ChainSmem& sm, const T (&v)[NV], int& pub) {
     double tot[NV];
-    block_sum_multi<T, NV>(v, tot, sm.red);
+    block_sum_exact<T, NV>(v, tot, sm.red);
     const int slot = pub & 1;
     ++pub;
     if (threadIdx.x == 0)
@@ -132,6 +132,7 @@ __global__ void __launch_bounds__(32) k_exchange_plain(DevBatch a) {
             const double lnA = (beta[i + 1] - beta[i]) * (sm.H[i + 1] - sm.H[i]);
             const uint4 w = rng_words(a.seed, (uint32_t)cd.s, (uint32_t)i, (uint32_t)cd.copy, step, 1u);
             a.prop[cd.pair_off + i] += 1;
+            xlog_write(a, cd.pair_off + i, lnA, 0.0, 0.0);
             if (metropolis(lnA, u53(w.x, w.y))) {
                 a.acc[cd.pair_off + i] += 1;
                 int t = sm.buf[i]; sm.buf[i] = sm.buf[i + 1]; sm.buf[i + 1] = t;
@@ -235,6 +236,7 @@ __device__ __forceinline__ void decimation_chain(const DevBatch& a, cg::cluster_
         cluster_sum<T, 1>(cl, sm, part, pub);
         if (threadIdx.x == 0) {
             const double lnA = sm.sum[0];
+            if (rank == 0) xlog_write(a, cd.pair_off + i, lnA, 0.0, 0.0);
             const bool ok = metropolis(lnA, pd.u[i]);
             sm.flag = ok;
             if (ok) {
@@ -320,19 +322,21 @@ __global__ void __launch_bounds__(EX_THREADS) k_exchange_coolheat(DevBatch a) {
         const T* s2 = pool + (long long)sm.buf[i + 1] * rep;
         T* f1 = pool + (long long)sm.free0 * rep;
         T* f2 = pool + (long long)sm.free1 * rep;
-        T v[4] = {(T)0, (T)0, (T)0, (T)0};  // ln J_C(s1), ln J_C(C^-1 s2), H[C s1], H[C^-1 s2]
+        // ln J_C(s1), ln J_C(C^-1 s2), H[C s1], H[C^-1 s2] (threads may hold
+        // many sites: two-sum accumulation, v + vc)
+        T v[4] = {(T)0, (T)0, (T)0, (T)0}, vc[4] = {(T)0, (T)0, (T)0, (T)0};
         // phase 1: cool colour 0 of s1 (neighbours: s1 colour 1);
         //          heat colour 1 of s2 (neighbours: s2 colour 0)
         for (int h = lo + (int)threadIdx.x; h < hi; h += blockDim.x) {
             const Site st0 = site_of(sd, 0, h);
             const V3<T> S = local_field<T>(st0, half, s1 + 3 * half, J0, J1);
             V3<T> s = ld3(s1, half, h);
-            v[0] += cool_site<T>(eps, S, s);
+            acc_add(v[0], vc[0], cool_site<T>(eps, S, s));
             st3(f1, half, h, s);
             const Site st1 = site_of(sd, 1, h);
             const V3<T> S2 = local_field<T>(st1, half, s2, J1, J0);
             V3<T> u = ld3(s2 + 3 * half, half, h);
-            v[1] += heat_site<T>(eps, S2, u);
+            acc_add(v[1], vc[1], heat_site<T>(eps, S2, u));
             st3(f2 + 3 * half, half, h, u);
         }
         __threadfence();
@@ -343,16 +347,18 @@ __global__ void __launch_bounds__(EX_THREADS) k_exchange_coolheat(DevBatch a) {
             const Site st1 = site_of(sd, 1, h);
             const V3<T> S = local_field<T>(st1, half, f1, J1, J0);
             V3<T> s = ld3(s1 + 3 * half, half, h);
-            v[0] += cool_site<T>(eps, S, s);
+            acc_add(v[0], vc[0], cool_site<T>(eps, S, s));
             st3(f1 + 3 * half, half, h, s);
-            v[2] -= dot(s, S);
+            acc_add(v[2], vc[2], -dot(s, S));
             const Site st0 = site_of(sd, 0, h);
             const V3<T> S2 = local_field<T>(st0, half, f2 + 3 * half, J0, J1);
             V3<T> u = ld3(s2, half, h);
-            v[1] += heat_site<T>(eps, S2, u);
+            acc_add(v[1], vc[1], heat_site<T>(eps, S2, u));
             st3(f2, half, h, u);
-            v[3] -= dot(u, S2);
+            acc_add(v[3], vc[3], -dot(u, S2));
         }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] += vc[k];
         cluster_sum<T, 4>(cl, sm, v, pub);
         if (threadIdx.x == 0) {
             const double LJ1 = sm.sum[0], LJ2 = sm.sum[1], HC = sm.sum[2], HH = sm.sum[3];
@@ -362,6 +368,7 @@ __global__ void __launch_bounds__(EX_THREADS) k_exchange_coolheat(DevBatch a) {
             if (rank == 0) {
                 a.prop[cd.pair_off + i] += 1;
                 if (ok) a.acc[cd.pair_off + i] += 1;
+                xlog_write(a, cd.pair_off + i, lnA, LJ1, LJ2);
             }
             if (ok) {
                 const int o1 = sm.buf[i], o2 = sm.buf[i + 1];

@@ -1,8 +1,18 @@
 // exchange_common.cuh -- helpers shared by the exchange kernels.
 #pragma once
+#include "kernels.h"
 #include "pt_device.cuh"
 
 namespace ptk {
+
+// Record a pair's log acceptance ratio and, for cooling/heating, its two
+// Jacobian terms (read back by pt_get_exchange_log).
+__device__ __forceinline__ void xlog_write(const DevBatch& a, long long pair, double lnA, double lj1, double lj2) {
+    double* p = a.xlog + 3 * pair;
+    p[0] = lnA;
+    p[1] = lj1;
+    p[2] = lj2;
+}
 
 // Per-pair constants of the decimation ratio (section III.A, Appendix A),
 // computed once per launch in double and rounded to the sweep precision T:

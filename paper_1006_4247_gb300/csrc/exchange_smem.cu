@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(HP_THREADS) k_heat_pre(DevBatch a) {
     if (v2) ch_colour<T, 2, false, true>(sd, out, src, out, J0, J1, 0, eps, part[0], part[1]);
     else ch_colour<T, 1, false, true>(sd, out, src, out, J0, J1, 0, eps, part[0], part[1]);
     double tot[2];
-    block_sum_multi<T, 2>(part, tot, red);
+    block_sum_exact<T, 2>(part, tot, red);
     if (threadIdx.x == 0) {
         a.heat_lnJ[pair] = tot[0];
         a.heat_H[pair] = tot[1];
@@ -211,13 +211,14 @@ __global__ void __launch_bounds__(SX_THREADS, 1) k_exchange_coolheat_smem(DevBat
         if (v2) ch_colour<T, 2, true, true>(sd, f1, s1, f1, J0, J1, 1, eps, part[0], part[1]);
         else ch_colour<T, 1, true, true>(sd, f1, s1, f1, J0, J1, 1, eps, part[0], part[1]);
         double tot[2];
-        block_sum_multi<T, 2>(part, tot, sm.red);
+        block_sum_exact<T, 2>(part, tot, sm.red);
         const long long pair = cd.pair_off + i;
         if (threadIdx.x == 0) {
             const double LJ1 = tot[0], HC = tot[1];
             const double HH = pHH[i], LJ2 = pLJ[i];
             const double b1 = pbeta[i], b2 = pbeta[i + 1];
             const double lnA = -b2 * HC - b1 * HH + b1 * sm.H[i] + b2 * sm.H[i + 1] + LJ1 - LJ2;
+            xlog_write(a, pair, lnA, LJ1, LJ2);
             const bool ok = sx_metropolis(lnA, pd.u[i]);
             sm.flag = ok;
             if (ok) {
@@ -298,9 +299,10 @@ __global__ void __launch_bounds__(SX_THREADS, 1) k_exchange_decimation_smem(DevB
             part[0] += sx_decim_D<T>(na, b1t, b2t, dbt, lr) - sx_decim_D<T>(nb, b1t, b2t, dbt, lr);
         }
         double tot1[1];
-        block_sum_multi<T, 1>(part, tot1, sm.red);
+        block_sum_exact<T, 1>(part, tot1, sm.red);
         const double lnA = tot1[0];
         if (threadIdx.x == 0) {
+            xlog_write(a, cd.pair_off + i, lnA, 0.0, 0.0);
             const bool ok = sx_metropolis(lnA, pd.u[i]);
             sm.flag = ok;
             if (ok) {
@@ -329,7 +331,7 @@ __global__ void __launch_bounds__(SX_THREADS, 1) k_exchange_decimation_smem(DevB
                 e12[1] -= dot(sb, Sb);
             }
             double E[2];
-            block_sum_multi<T, 2>(e12, E, sm.red);
+            block_sum_exact<T, 2>(e12, E, sm.red);
             if (threadIdx.x == 0) {
                 sm.H[i] = E[0];
                 sm.H[i + 1] = E[1];

@@ -76,6 +76,10 @@ struct DevBatch {
     void* heat_buf;
     double* heat_H;
     double* heat_lnJ;
+    // [pairs][3]: ln A, ln det J_C(s1), ln det J_C(C^-1 s2) of each pair's
+    // most recent proposal (the two Jacobian terms are 0 for the standard
+    // and decimation swaps)
+    double* xlog;
 };
 
 // Record the text returned by pt_last_error() for the calling thread.

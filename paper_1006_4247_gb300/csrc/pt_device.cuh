@@ -128,23 +128,13 @@ template <> struct M<double> {
     static constexpr double pi = CUDART_PI;
 };
 
-// Math of the cooling / heating transforms.  In float the hardware
-// approximations are used for sin, cos and log (arguments stay in [-pi, pi],
-// absolute error ~2^-21); the double path keeps the accurate library calls.
+// Quotients of the cooling / heating transforms.  Float uses the hardware
+// reciprocal quotient (2 ulp; operands O(1) or small angles); double divides.
 template <typename T> struct MX;
 template <> struct MX<float> {
-    static __device__ __forceinline__ void sincos_(float x, float* s, float* c) { __sincosf(x, s, c); }
-    static __device__ __forceinline__ float sin_(float x) { return __sinf(x); }
-    static __device__ __forceinline__ float cos_(float x) { return __cosf(x); }
-    static __device__ __forceinline__ float log_(float x) { return __logf(x); }
-    // hardware reciprocal quotient (2 ulp); operands here are O(1) or small angles
     static __device__ __forceinline__ float div_(float a, float b) { return __fdividef(a, b); }
 };
 template <> struct MX<double> {
-    static __device__ __forceinline__ void sincos_(double x, double* s, double* c) { sincos(x, s, c); }
-    static __device__ __forceinline__ double sin_(double x) { return sin(x); }
-    static __device__ __forceinline__ double cos_(double x) { return cos(x); }
-    static __device__ __forceinline__ double log_(double x) { return log(x); }
     static __device__ __forceinline__ double div_(double a, double b) { return a / b; }
 };
 
@@ -153,18 +143,22 @@ template <typename T> struct V3 { T x, y, z; };
 template <typename T>
 __device__ __forceinline__ T dot(const V3<T>& a, const V3<T>& b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
 
-// s <- s / |s|.  Every caller rotates, reflects or builds a unit vector, so
-// |s|^2 = 1 + d with d a few rounding errors.  In double the factor is then
-// taken from the first Newton step for x^(-1/2) at x = 1, 1 - d/2, whose
-// error 3d^2/8 is below the rounding of the result for |d| < 1e-8: two
-// instructions instead of a square root and a division on GB300's slow FP64
-// pipe; larger |d| (never seen) take the exact factor.  Float uses the
-// hardware reciprocal square root.
+// s <- s / |s|.  Every caller rotates, reflects or builds a unit vector from
+// unit vectors (spins enter the engine normalised: pt_set_spins normalises,
+// initial spins are unit), so |s|^2 = 1 + d with d a few rounding errors.  The
+// factor is then the first Newton step for x^(-1/2) at x = 1, 1 - d/2 (one
+// FMA), whose error 3d^2/8 is below the result's rounding.  Float always takes
+// it: it replaces the hardware reciprocal square root, whose error has a sign
+// bias (renormalising with it left |s|^2 - 1 at -8e-8 on average, i.e. spins
+// a little short and energies scaled by 1 - 8e-8), while one rounded FMA
+// rounds both ways.  Double guards |d| < 1e-8 and otherwise divides by the
+// square root; the Newton form saves a square root and a division on GB300's
+// slow FP64 pipe.
 template <typename T>
 __device__ __forceinline__ void renorm(V3<T>& s) {
     const T ss = dot(s, s);
     T inv;
-    if (sizeof(T) == 8 && fabs(ss - (T)1) < (T)1e-8) inv = (T)1.5 - (T)0.5 * ss;
+    if (sizeof(T) == 4 || fabs(ss - (T)1) < (T)1e-8) inv = (T)1.5 - (T)0.5 * ss;
     else inv = M<T>::rsqrt_(ss);
     s.x *= inv; s.y *= inv; s.z *= inv;
 }
@@ -287,8 +281,58 @@ __device__ __forceinline__ T ln_sinhc(T R) {
     return R + M<T>::log1p_(-M<T>::exp_((T)-2 * R)) - M<T>::log_((T)2 * R);
 }
 
+// Rotation angle functions of the cooling and heating steps: cos(a) - 1 and
+// sin(a) / a.  The angle obeys 0 <= a <= eps |S| < 1 (the invertibility
+// bound of section III.B), so in float both are taken from their Taylor
+// series, truncated after the a^10 term (remainder below a^12 / 12! and
+// a^12 / 13!, i.e. under 2.1e-9 relative on [0, 1)): they keep full relative
+// accuracy at the small angles of the method, where cos(a) - 1 would lose
+// every digit to cancellation and the hardware sine has an absolute, not a
+// relative, error.  Double uses the library functions.
+template <typename T> struct Rot;
+template <> struct Rot<float> {
+    static __device__ __forceinline__ void cs(float a, float& cm1, float& sc) {
+        const float a2 = a * a;
+        // cos a - 1 = -a^2/2! + a^4/4! - a^6/6! + a^8/8! - a^10/10!
+        float c = -2.7557319e-7f;
+        c = fmaf(c, a2, 2.4801587e-5f);
+        c = fmaf(c, a2, -1.3888889e-3f);
+        c = fmaf(c, a2, 4.1666668e-2f);
+        c = fmaf(c, a2, -0.5f);
+        cm1 = c * a2;
+        // sin a / a = 1 - a^2/3! + a^4/5! - a^6/7! + a^8/9! - a^10/11!
+        float t = -2.5052108e-8f;
+        t = fmaf(t, a2, 2.7557319e-6f);
+        t = fmaf(t, a2, -1.9841270e-4f);
+        t = fmaf(t, a2, 8.3333333e-3f);
+        t = fmaf(t, a2, -0.16666667f);
+        sc = fmaf(t, a2, 1.0f);
+    }
+};
+template <> struct Rot<double> {
+    static __device__ __forceinline__ void cs(double a, double& cm1, double& sc) {
+        cm1 = cos(a) - 1.0;
+        sc = a == 0.0 ? 1.0 : sin(a) / a;
+    }
+};
+
+// ln det J_f of one elementary step, ln[(1 - q)(cos a - q sin(a)/a)], with
+// q = eps (S.s) (cooling) or e cos(theta) (heating, at the pre-image).  In
+// float the product is written as 1 + x with x = d - q - q d,
+// d = (cos a - 1) - q sin(a)/a, and the logarithm taken as log1p(x): every
+// quantity is formed at the size it has (x is small), so the per-site value
+// is accurate to a few units in the last place of x instead of carrying the
+// absolute error of a logarithm near 1, which summed over N sites would bias
+// ln det J_C by O(N 1e-7).  Double keeps ln|j| of the product (the oracle's
+// form).
 template <typename T>
-__device__ __forceinline__ T sinc_(T a) { return a == (T)0 ? (T)1 : MX<T>::div_(MX<T>::sin_(a), a); }
+__device__ __forceinline__ T ln_jac(T q, T ca, T cm1, T sc) {
+    if (sizeof(T) == 4) {
+        const T d = cm1 - q * sc;
+        return M<T>::log1p_(d - q - q * d);
+    }
+    return M<T>::log_(fabs(((T)1 - q) * (ca - q * sc)));
+}
 
 // Cooling step (section III.B): rotate s towards S by alpha = eps |p|,
 // p = S - (S.s) s; returns ln det J_f = ln[(1 - eps S.s)(cos a - eps S.s sinc a)].
@@ -298,14 +342,15 @@ __device__ __forceinline__ T cool_site(T eps, const V3<T>& S, V3<T>& s) {
     const V3<T> p = {S.x - sS * s.x, S.y - sS * s.y, S.z - sS * s.z};
     const T pn = M<T>::sqrt_(dot(p, p));
     const T alpha = eps * pn;
-    const T ca = MX<T>::cos_(alpha), sc = sinc_(alpha);
-    const T j = ((T)1 - eps * sS) * (ca - eps * sS * sc);
+    T cm1, sc;
+    Rot<T>::cs(alpha, cm1, sc);
+    const T ca = (T)1 + cm1;
     const T f = eps * sc;
     s.x = s.x * ca + p.x * f;
     s.y = s.y * ca + p.y * f;
     s.z = s.z * ca + p.z * f;
     renorm(s);
-    return MX<T>::log_(fabs(j));
+    return ln_jac<T>(eps * sS, ca, cm1, sc);
 }
 
 // Heating step = inverse cooling step: theta' (angle between s' and S) given,
@@ -327,14 +372,17 @@ __device__ __forceinline__ T heat_site(T eps, const V3<T>& S, V3<T>& s) {
     const T inv = nS > (T)0 ? MX<T>::div_((T)1, nS) : (T)0;
     const T cp = nS > (T)0 ? sS * inv : (T)1;  // cos(theta')
     const T sp = pn * inv;                     // sin(theta')
-    T alpha = e * sp, sa, ca;
-    MX<T>::sincos_(alpha, &sa, &ca);
+    T alpha = e * sp, cm1, sc;
+    Rot<T>::cs(alpha, cm1, sc);
+    T sa = alpha * sc, ca = (T)1 + cm1;
     for (int it = 0; it < M<T>::newton_max; ++it) {
         // f = alpha - e sin(theta' + alpha), f' = 1 - e cos(theta' + alpha)
         const T sth = sp * ca + cp * sa, cth = cp * ca - sp * sa;
         const T d = MX<T>::div_(alpha - e * sth, (T)1 - e * cth);  // only the path to the root
         alpha -= d;
-        MX<T>::sincos_(alpha, &sa, &ca);
+        Rot<T>::cs(alpha, cm1, sc);
+        sa = alpha * sc;
+        ca = (T)1 + cm1;
         if (fabs(d) < M<T>::newton_tol) break;
     }
     if (pn > (T)0) {
@@ -345,9 +393,7 @@ __device__ __forceinline__ T heat_site(T eps, const V3<T>& S, V3<T>& s) {
         renorm(s);
     }
     const T cth = cp * ca - sp * sa;  // cos(theta)
-    const T sinc = alpha == (T)0 ? (T)1 : MX<T>::div_(sa, alpha);
-    const T j = ((T)1 - e * cth) * (ca - e * cth * sinc);
-    return MX<T>::log_(fabs(j));
+    return ln_jac<T>(e * cth, ca, cm1, sc);
 }
 
 // ---------------------------------------------------------------------------
@@ -525,6 +571,57 @@ __device__ __forceinline__ void block_sum_multi(const T (&v)[NV], double (&out)[
                 double r = (lane < nw) ? (double)shT[k * 32 + lane] : 0.0;
                 out[k] = warp_sum(r);
             }
+        }
+    }
+}
+
+// Knuth's two-sum accumulation: s + c carries the running sum of the added
+// values to about twice the working precision (for threads that add many
+// site terms before the block reduction).
+template <typename T>
+__device__ __forceinline__ void acc_add(T& s, T& c, T x) {
+    const T t = s + x;
+    const T bp = t - s;
+    c += (s - (t - bp)) + (x - bp);
+    s = t;
+}
+
+// Sum of NV per-thread values over the CTA for the exchange kernels.  Their
+// totals (energies of proposals, ln det J_C, decimation sums) enter ln A
+// multiplied by beta, and partial sums reach 10^3..10^4, where a float
+// shuffle tree would lose ~1e-4 per warp.  Float values are therefore turned
+// into 64-bit fixed point once per thread (resolution 2^-32; |total| < 2^31
+// by far) and added exactly: integer addition is associative, so the result
+// is the exact sum of the per-thread values for any reduction order or
+// cluster size, rounded once to double (exactly, while |total| < 2^21).  The
+// adds run on the integer pipe, not GB300's slow FP64 one.  Double values
+// take block_sum_multi.  Results valid in warp 0; sh holds NV * 32 doubles.
+template <typename T, int NV>
+__device__ __forceinline__ void block_sum_exact(const T (&v)[NV], double (&out)[NV], double* sh) {
+    if (sizeof(T) == 8) {
+        block_sum_multi<T, NV>(v, out, sh);
+        return;
+    }
+    static_assert(NV <= 32, "one slot row per value");
+    long long* shI = reinterpret_cast<long long*>(sh);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        long long x = __float2ll_rn((float)v[k] * 4294967296.0f);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xFFFFFFFFu, x, o);
+        if (lane == 0) shI[k * 32 + wid] = x;
+    }
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    if (wid == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            long long r = (lane < nw) ? shI[k * 32 + lane] : 0ll;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xFFFFFFFFu, r, o);
+            out[k] = (double)r * 0x1p-32;
         }
     }
 }

@@ -35,9 +35,11 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 # against the header).
 ENTRY_POINTS = ["pt_options_default", "pt_create", "pt_create_batch", "pt_sweep", "pt_sweep_samples",
                 "pt_cycles", "pt_autotune", "pt_get_paths", "pt_set_paths", "pt_exchange",
-                "pt_measure", "pt_measure_device", "pt_get_stats", "pt_get_spins", "pt_set_spins",
+                "pt_measure", "pt_measure_device", "pt_get_stats", "pt_get_exchange_log", "pt_get_spins",
+                "pt_set_spins",
                 "pt_set_params", "pt_set_rng_step", "pt_get_rng_step", "pt_save", "pt_load",
                 "pt_profile", "pt_profile_read", "pt_set_policy", "pt_set_wait_limit", "pt_energy_noalloc",
+                "pt_smem_bandwidth",
                 "pt_destroy",
                 "pt_last_error", "pt_mlp_create", "pt_mlp_num_params", "pt_mlp_set_params",
                 "pt_mlp_get_params", "pt_mlp_forward", "pt_mlp_loss_grad", "pt_mlp_train", "pt_mlp_ladder",
@@ -94,7 +96,9 @@ def load_library(path: str = LIB_PATH):
                 "pt_set_policy": (ip, [vp, ip]),
                 "pt_set_wait_limit": (ip, [vp, C.c_ulonglong, ip]),
                 "pt_energy_noalloc": (ip, [vp, ip, ip, ip, vp, vp, vp]),
+                "pt_smem_bandwidth": (ip, [vp, dp, dp, dp]),
                 "pt_get_stats": (ip, [vp, i64p, i64p, i64p, i32p]),
+                "pt_get_exchange_log": (ip, [vp, dp, dp]),
                 "pt_get_spins": (ip, [vp, ip, ip, ip, dp]),
                 "pt_set_spins": (ip, [vp, ip, ip, ip, dp]),
                 "pt_set_params": (ip, [vp, dp, fp]),
@@ -251,9 +255,21 @@ def pt_energy_noalloc(d_spins, precision, L, n_configs, d_couplings, d_energy, s
                                             d_energy, stream))
 
 
+def pt_smem_bandwidth(stream=None):
+    """(bytes/s over all SMs, bytes per clock per SM, SM MHz) of the measured
+    shared-memory load stream on the current device."""
+    out = [C.c_double(), C.c_double(), C.c_double()]
+    _check(load_library().pt_smem_bandwidth(stream, *[C.byref(o) for o in out]))
+    return tuple(o.value for o in out)
+
+
 def pt_get_stats(h, proposals=None, accepts=None, round_trips=None, perm=None):
     _check(load_library().pt_get_stats(h, _ptr(proposals, C.c_int64), _ptr(accepts, C.c_int64),
                                        _ptr(round_trips, C.c_int64), _ptr(perm, C.c_int32)))
+
+
+def pt_get_exchange_log(h, lnA=None, lnJ=None):
+    _check(load_library().pt_get_exchange_log(h, _ptr(lnA, C.c_double), _ptr(lnJ, C.c_double)))
 
 
 def pt_get_spins(h, sample, copy, replica, out):
@@ -477,6 +493,17 @@ class Engine:
             return (prop.reshape(self.S, self.C, NT - 1), acc.reshape(self.S, self.C, NT - 1),
                     rt.reshape(self.S, self.C), perm.reshape(self.S, self.C, NT))
         return prop, acc, rt, perm
+
+    def exchange_log(self):
+        """(ln A, ln det J terms) of every pair's most recent proposal; shapes
+        [S][C][NT-1] and [S][C][NT-1][2] for a uniform batch, flat otherwise."""
+        lnA = np.zeros(self.P)
+        lnJ = np.zeros(2 * self.P)
+        pt_get_exchange_log(self.h, lnA, lnJ)
+        if self.uniform:
+            NT = self.NT[0]
+            return lnA.reshape(self.S, self.C, NT - 1), lnJ.reshape(self.S, self.C, NT - 1, 2)
+        return lnA, lnJ.reshape(-1, 2)
 
     def get_spins(self, sample, copy, replica):
         out = np.zeros((self.L[sample] ** 3, 3))

@@ -50,6 +50,31 @@ def test_checkpoint_resume_is_exact(tmp_path, mode, precision):
     b.close()
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_set_spins_normalises_and_rejects_zero(precision):
+    """Spins enter the engine as unit vectors (the updates' renormalisation
+    only corrects rounding): pt_set_spins scales spins of other lengths to
+    unit length, keeps unit ones as given, and refuses a zero spin, leaving
+    the stored configuration unchanged."""
+    L = 4
+    eng, J, B = make_engine(L, 1, 3, 2, precision)
+    v = W.random_spins(L, 5) * np.linspace(0.5, 3.0, L ** 3)[:, None]
+    eng.set_spins(0, 1, 2, v)
+    got = eng.get_spins(0, 1, 2)
+    tol = 1e-15 if precision == "fp64" else 1e-7
+    assert np.abs(np.linalg.norm(got, axis=1) - 1.0).max() <= 2 * tol
+    assert np.abs(got - v / np.linalg.norm(v, axis=1, keepdims=True)).max() <= 2 * tol
+    eng.set_spins(0, 1, 2, got)  # unit to float accuracy: stored bit for bit
+    assert (eng.get_spins(0, 1, 2) == got).all()
+    bad = got.copy()
+    bad[7] = 0.0
+    with pytest.raises(pt.PtError) as ei:
+        eng.set_spins(0, 1, 2, bad)
+    assert ei.value.status == pt.PT_ERR_ARG and "zero" in str(ei.value)
+    assert (eng.get_spins(0, 1, 2) == got).all()
+    eng.close()
+
+
 def test_error_statuses():
     eng, J, B = make_engine(4, 1, 3, 2, "fp32")
     with pytest.raises(pt.PtError) as ei:

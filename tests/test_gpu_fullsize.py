@@ -22,7 +22,7 @@ import numpy as np
 import pytest
 
 import oracle as orc
-from gpu_util import ambiguous_basis_sites, site_colour
+from gpu_util import ambiguous_basis_sites, check_float_walk, exchange_walk, float_tolerances, site_colour
 from paper_1006_4247_gb300 import pt
 from paper_1006_4247_gb300 import workloads as W
 
@@ -122,12 +122,25 @@ def test_fullsize_exchange_sampled(name, chains):
         ch.label[:] = perm[s, c]
         ref[(s, c)] = (ch, perm[s, c].copy(), acc[s, c].copy())
     step = eng.step
+    H0 = eng.energies()
+    eps = np.full(NT - 1, w.eps, np.float32)
     eng.exchange(w.exchange)
     prop, acc, rt, perm = eng.stats()
     H = eng.energies()
+    # the logged ln A (and ln det J_C terms) of every pair against the oracle
+    # walk that follows the engine's decisions, up to the first re-insertion
+    # where float and double may part
+    lnA, lnJ = eng.exchange_log()
+    errors = {}
+    for (s, c), (ch, _, _) in ref.items():
+        recs = exchange_walk(w.exchange, L, J[s], B[s], ch.spins, H0[s, c], 7, s, c, step, eps=eps,
+                             follow_lnA=lnA[s, c])[0]
+        float_tolerances(recs, w.exchange, B[s], L ** 3)
+        check_float_walk(errors, name, lnA[s, c], lnJ[s, c], recs, L ** 3)
+    print(f"\n{name} exchange log vs oracle walk:", errors[name])
     mismatched = 0
     for (s, c), (ch, perm0, acc0) in ref.items():
-        ch.exchange(mode, step, eps=np.full(NT - 1, w.eps))
+        ch.exchange(mode, step, eps=eps)
         got_acc = acc[s, c] - acc0
         if not (perm[s, c] == ch.label).all() or not (got_acc == ch.acc).all():
             mismatched += 1
@@ -177,4 +190,58 @@ def test_fullsize_uneven_batch_sampled():
         L, NT = w.L[s], w.n_replicas[s]
         Hr = orc.energy(L, np.asarray(Js[s], np.float64), eng.get_spins(s, c, b))
         assert abs(H[off[s] + c * NT + b] - Hr) <= 2e-5 * abs(Hr)
+    eng.close()
+
+
+def test_fullsize_L24_coolheat_cluster_exchange_sampled():
+    """Cooling/heating at L = 24 in float, the size the paper's second
+    protocol runs (10 coupling sets x 27 replicas x 2 copies on the geometric
+    ladder, cooling parameter kappa = 0.1): its configurations do not fit one
+    SM, so the exchange runs as the cluster kernel (one launch, no heating
+    pre-pass), after autotuned sweeps.  Sampled chains: per pair ln A and the
+    two ln det J_C terms against the oracle walk within the float bounds,
+    decisions equal outside the round-off band, the final configurations to
+    1e-5 per component."""
+    L, S, NT, seed = 24, 10, 27, 17
+    J = np.stack([W.couplings(L, 8000 + 97 * L + k) for k in range(S)])
+    B = np.stack([W.geometric_betas(NT)] * S)
+    eps = np.stack([(0.1 * np.log(B[s, 1:] / B[s, :-1])).astype(np.float32) for s in range(S)])
+    eng = pt.Engine(L, J, B, n_copies=2, precision="fp32", seed=seed)
+    eng.set_params(eps=eps)
+    eng.autotune(1, 30)
+    choice, _ = eng.paths()
+    assert (choice >= 10).all()
+    for _ in range(3):
+        eng.sweep(1, 30)
+        eng.exchange("coolheat")
+    eng.sweep(1, 30)
+    Jd = J.astype(np.float64)
+    N = L ** 3
+    chains = [(2, 0), (7, 1)]
+    H0 = eng.energies()
+    step = eng.step
+    start = {(s, c): np.stack([eng.get_spins(s, c, b) for b in range(NT)]) for (s, c) in chains}
+    perm0 = eng.stats()[3]
+    eng.profile(True)
+    eng.exchange("coolheat")
+    _, launches = eng.profile_read()
+    eng.profile(False)
+    assert launches["exchange"] == 1  # the cluster kernel, no heating pre-pass
+    perm1 = eng.stats()[3]
+    lnA, lnJ = eng.exchange_log()
+    errors = {}
+    n_acc = 0
+    for (s, c) in chains:
+        recs, sp, Hw, permw = exchange_walk("coolheat", L, Jd[s], B[s], start[(s, c)], H0[s, c], seed, s, c, step,
+                                            eps=eps[s], follow_lnA=lnA[s, c])
+        float_tolerances(recs, "coolheat", B[s], N)
+        assert check_float_walk(errors, "L24", lnA[s, c], lnJ[s, c], recs, N)
+        assert (perm1[s, c] == perm0[s, c][permw]).all()
+        for b in range(NT):
+            d = np.abs(eng.get_spins(s, c, b) - sp[b]).max()
+            errors["L24"]["spin"] = max(errors["L24"]["spin"], float(d))
+            assert d <= 1e-5, (s, c, b, d)
+        n_acc += sum(bool(r["accepted"]) for r in recs)
+    print("\nL=24 cluster cooling/heating, float vs oracle:", errors["L24"], "accepted pairs", n_acc)
+    assert n_acc > 0
     eng.close()

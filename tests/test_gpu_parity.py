@@ -11,7 +11,8 @@ import numpy as np
 import pytest
 
 import oracle as orc
-from gpu_util import ambiguous_basis_sites, get_state, make_engine, set_random_state, site_colour
+from gpu_util import (ambiguous_basis_sites, check_float_walk, exchange_walk, float_tolerances, get_state,
+                      make_engine, set_random_state, site_colour)
 
 pytestmark = pytest.mark.gpu
 
@@ -147,25 +148,41 @@ def _oracle_chains(eng_state, J, B, S, C, NT, L, seed):
     return chains
 
 
-@pytest.mark.parametrize("mode", ["plain", "decimation", "coolheat"])
+# Exchange kernels: "auto" runs the staged kernels (the pair in shared memory;
+# k_heat_pre + k_exchange_coolheat_smem, k_exchange_decimation_smem) at these
+# sizes; "l2:<n>" forces the cluster kernels (k_exchange_coolheat,
+# k_exchange_decimation) with n CTAs per chain, the ones float batches with
+# L > 20 and double batches with L > 16 run.
+EXCHANGE_IMPLS = {"auto": {}, "l2:1": {"PT_EXCHANGE_IMPL": "l2", "PT_EXCHANGE_CLUSTER": "1"},
+                  "l2:2": {"PT_EXCHANGE_IMPL": "l2", "PT_EXCHANGE_CLUSTER": "2"},
+                  "l2:4": {"PT_EXCHANGE_IMPL": "l2", "PT_EXCHANGE_CLUSTER": "4"}}
+EXCHANGE_CASES = [("plain", "auto")] + [(m, i) for m in ("decimation", "coolheat") for i in EXCHANGE_IMPLS]
+
+
+@pytest.mark.parametrize("mode,impl", EXCHANGE_CASES)
 @pytest.mark.parametrize("L", [4, 6, 12])
-def test_exchange_fp64(mode, L):
+def test_exchange_fp64(mode, impl, L):
     """One tempering update from identical state: permutation, counters,
     round trips bit-exact; spins (re-inserted or transformed) to 1e-12;
-    energies to 1e-11."""
+    energies to 1e-11; the logged ln A (and the two ln det J_C terms of
+    cooling/heating) of every pair to 1e-9 of the oracle walk's."""
     S, C, NT, seed = 2, 2, 6, 31
-    eng, J, B = make_engine(L, S, NT, C, "fp64", seed=seed, bmin=1.8, bmax=2.4)
+    eng, J, B = _engine_env(EXCHANGE_IMPLS[impl], L, S, NT, C, "fp64", seed=seed, bmin=1.8, bmax=2.4)
     st = set_random_state(eng, S, C, NT, L, seed=29)
     chains = _oracle_chains(st, J, B, S, C, NT, L, seed)
     eps = np.full((S, NT - 1), 0.02, np.float32)
     for rnd in range(4):
         step = eng.step
+        H0 = eng.energies()
+        walks = [exchange_walk(mode, L, J[s], B[s], get_state(eng, S, C, NT)[s, c], H0[s, c], seed, s, c, step,
+                               eps=eps[s]) for s in range(S) for c in range(C)]
         eng.exchange(mode, eps if mode == "coolheat" else None)
         for ch in chains:
             ch.exchange({"plain": 0, "decimation": 1, "coolheat": 2}[mode], step, eps=eps[0])
         prop, acc, rt, perm = eng.stats()
         H = eng.energies()
         out = get_state(eng, S, C, NT)
+        lnA, lnJ = eng.exchange_log()
         for s in range(S):
             for c in range(C):
                 ch = chains[s * C + c]
@@ -174,6 +191,11 @@ def test_exchange_fp64(mode, L):
                 assert rt[s, c] == ch.rt_count[0]
                 assert np.abs(out[s, c] - ch.spins).max() <= 1e-12
                 assert np.abs(H[s, c] - ch.H).max() <= 1e-11 * max(1.0, np.abs(ch.H).max())
+                recs = walks[s * C + c][0]
+                for i, r in enumerate(recs):
+                    assert abs(lnA[s, c, i] - r["lnA"]) <= 1e-9 * max(1.0, abs(r["lnA"])), (rnd, s, c, i)
+                    assert abs(lnJ[s, c, i, 0] - r["lnJ1"]) <= 1e-9 * max(1.0, abs(r["lnJ1"]))
+                    assert abs(lnJ[s, c, i, 1] - r["lnJ2"]) <= 1e-9 * max(1.0, abs(r["lnJ2"]))
         # move the state on and start the next update from an identical state
         # (the oracle takes the engine's spins; its bookkeeping continues)
         eng.sweep(0, 1)
@@ -185,6 +207,62 @@ def test_exchange_fp64(mode, L):
                 for b in range(NT):
                     ch.H[b] = orc.energy(L, ch.J, ch.spins[b])
     assert sum(int(c.acc.sum()) for c in chains) > 0
+    eng.close()
+
+
+FLOAT_ERRORS = {}
+
+
+# decimation re-inserts sites by heat bath, where float and double may orient
+# a site's basis oppositely (|S_z| < 1e-4 |S|, about one site in 10^4): kept to
+# L <= 8 so that the walks rarely part there
+FLOAT_WALK_CASES = [(m, i, L) for i in ("auto", "l2:2") for m, Ls in (("decimation", (6, 8)),
+                                                                        ("coolheat", (6, 8, 16))) for L in Ls]
+
+
+@pytest.mark.parametrize("mode,impl,L", FLOAT_WALK_CASES)
+def test_exchange_fp32_elementwise(mode, impl, L):
+    """Single precision decimation and cooling/heating, staged and cluster
+    kernels, one tempering update from an identical state: per pair ln A and
+    ln det J_C(s1), ln det J_C(C^-1 s2) against the oracle walk within the
+    bounds of gpu_util; decisions equal outside the round-off band of ln u
+    (the walk follows the engine inside it); the final configurations
+    (re-inserted, cooled and heated) to 1e-5 per component, the energies to
+    2e-5, the permutation exactly."""
+    S, C, NT, seed = 2, 2, 6, 43
+    eng, J, B = _engine_env(EXCHANGE_IMPLS[impl], L, S, NT, C, "fp32", seed=seed, bmin=1.8, bmax=2.4)
+    set_random_state(eng, S, C, NT, L, seed=47)
+    N = L ** 3
+    # a cooling parameter near the acceptance optimum of this ladder (kappa ~ 0.1)
+    eps = np.full((S, NT - 1), 0.1 * np.log(B[0, 1] / B[0, 0]), np.float32)
+    name = f"{mode}/{impl}"
+    compared = 0
+    for rnd in range(2):
+        step = eng.step
+        H0 = eng.energies()
+        state = get_state(eng, S, C, NT)
+        perm0 = eng.stats()[3]
+        eng.exchange(mode, eps if mode == "coolheat" else None)
+        perm1 = eng.stats()[3]
+        lnA, lnJ = eng.exchange_log()
+        out = get_state(eng, S, C, NT)
+        H = eng.energies()
+        for s in range(S):
+            for c in range(C):
+                recs, sp, Hw, permw = exchange_walk(mode, L, J[s], B[s], state[s, c], H0[s, c], seed, s, c, step,
+                                                    eps=eps[s], follow_lnA=lnA[s, c])
+                float_tolerances(recs, mode, B[s], N)
+                if not check_float_walk(FLOAT_ERRORS, name, lnA[s, c], lnJ[s, c], recs, N):
+                    continue
+                assert (perm1[s, c] == perm0[s, c][permw]).all(), (name, s, c)
+                d = float(np.abs(out[s, c] - sp).max())
+                FLOAT_ERRORS[name]["spin"] = max(FLOAT_ERRORS[name]["spin"], d)
+                assert d <= 1e-5, (name, s, c, d)
+                assert np.abs(H[s, c] - Hw).max() <= 2e-5 * np.abs(Hw).max()
+                compared += 1
+        eng.sweep(0, 1)
+    assert compared >= 2 * S * C - 2
+    print(f"\nfloat exchange errors vs oracle ({name}, L={L}):", FLOAT_ERRORS[name])
     eng.close()
 
 

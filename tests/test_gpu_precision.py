@@ -21,7 +21,7 @@ import numpy as np
 import pytest
 
 import oracle as orc
-from gpu_util import ambiguous_basis_sites, site_colour
+from gpu_util import ambiguous_basis_sites, check_float_walk, exchange_walk, float_tolerances, site_colour
 from paper_1006_4247_gb300 import pt
 from paper_1006_4247_gb300 import workloads as W
 
@@ -138,3 +138,56 @@ def test_paired_long_run_float_vs_double():
     print("\nprecision study, paired float - double:", json.dumps(out))
     z = np.concatenate(zs)
     assert (z < 2.0).mean() >= 0.85 and z.max() < 5.0
+
+
+def test_coolheat_errors_against_oracle():
+    """Cooling/heating at L = 16 (64 samples x 24 replicas x 2 copies, the
+    configuration-2 batch, staged exchange kernels; cooling parameter
+    kappa = 0.1, eps_i = kappa ln(beta_{i+1}/beta_i), so that about a third of
+    the pairs accept): one tempering update of sampled chains from an
+    identical state, float and double engines, against the oracle walk
+    (which follows the engine's decisions).  Reported per precision: the
+    largest error of a sweep's ln det J_C, of a pair's ln A, of a transformed
+    spin component, and the pairs decided differently (round-off ties)."""
+    name = "L16_R24_S64"
+    chains = [(4, 0), (21, 1), (50, 0), (63, 1)]
+    report = {}
+    for precision in ("fp32", "fp64"):
+        w = W.WORKLOADS[name]()
+        J = np.stack(w.couplings())
+        B = np.stack(w.betas())
+        eng = pt.Engine(w.L[0], J, B, n_copies=2, precision=precision, seed=5)
+        L, NT, S = w.L[0], w.n_replicas[0], w.n_samples
+        eps = np.stack([(0.1 * np.log(B[s, 1:] / B[s, :-1])).astype(np.float32) for s in range(S)])
+        eng.set_params(eps=eps)
+        Jd = J.astype(np.float64)
+        for _ in range(2):
+            eng.sweep(w.n_hb, w.n_or)
+            eng.exchange("coolheat")
+        eng.sweep(w.n_hb, w.n_or)
+        H0 = eng.energies()
+        step = eng.step
+        start = {(s, c): np.stack([eng.get_spins(s, c, b) for b in range(NT)]) for (s, c) in chains}
+        perm0 = eng.stats()[3]
+        eng.exchange("coolheat")
+        perm1 = eng.stats()[3]
+        lnA, lnJ = eng.exchange_log()
+        errors = {}
+        n_acc = 0
+        for (s, c) in chains:
+            recs, sp, Hw, permw = exchange_walk("coolheat", L, Jd[s], B[s], start[(s, c)], H0[s, c], 5, s, c, step,
+                                                eps=eps[s], follow_lnA=lnA[s, c])
+            float_tolerances(recs, "coolheat", B[s], L ** 3)
+            check_float_walk(errors, name, lnA[s, c], lnJ[s, c], recs, L ** 3)
+            assert (perm1[s, c] == perm0[s, c][permw]).all(), (precision, s, c)
+            d = max(float(np.abs(eng.get_spins(s, c, b) - sp[b]).max()) for b in range(NT))
+            errors[name]["spin"] = max(errors[name]["spin"], d)
+            n_acc += sum(bool(r["accepted"]) for r in recs)
+        errors[name]["accepted_pairs"] = int(n_acc)
+        report[precision] = errors[name]
+        eng.close()
+    print("\nprecision study, cooling/heating:", json.dumps(report))
+    assert report["fp64"]["ties"] == 0
+    assert report["fp64"]["lnA"] <= 1e-8 and report["fp64"]["lnJ"] <= 1e-9 and report["fp64"]["spin"] <= 1e-12
+    assert report["fp32"]["spin"] <= 1e-5 and report["fp32"]["lnJ"] <= 16 ** 3 * 1e-6
+    assert report["fp32"]["accepted_pairs"] > 0

@@ -1,0 +1,94 @@
+"""Long-run statistical parity with the FP64 oracle at the sizes of the
+benchmark batches (section IV's measurements: energy, acceptance per pair and
+the overlap susceptibility, errors from independent runs).
+
+  L = 16, 24 inverse temperatures linear in [2, 8], 1 heat-bath + 20
+  overrelaxation sweeps and one cooling/heating update (eps = 0.017) per
+  cycle, 150 cycles with the first 50 discarded (the configuration-2 batch);
+  L = 32, 48 inverse temperatures, 1 + 40 sweeps and one decimation update,
+  40 cycles with the first 10 discarded (the configuration-3 batch).
+
+Both sides run independent chain pairs of one coupling set from spins uniform
+on the sphere: the oracle's per-run averages are stored in tests/golden/ by
+tests/golden/make_stats_large.py (which calls only the oracle); the engine
+runs 64 chain pairs of the same set in one batch (one sample slot each, own
+Philox key).  The per-run averages over the kept cycles are independent
+draws of the same random variable on both sides whether or not the chains
+have equilibrated, so their means must agree within the combined standard
+error.  Rule, for the 3 N_T - 1 observables at once: at least 90% within
+2 sigma and all within 4 sigma.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_1006_4247_gb300 import pt
+from paper_1006_4247_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+GOLDEN = {16: "stats_L16_R24.json", 32: "stats_L32_R48.json"}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1006_4247_gb300 import _build
+    _build.build()
+
+
+def _golden(L):
+    with open(os.path.join(HERE, "golden", GOLDEN[L])) as fh:
+        return json.load(fh)
+
+
+def _gpu_runs(d, precision, S, seed):
+    L, NT = d["L"], d["NT"]
+    betas = np.array(d["betas"])
+    assert np.allclose(betas, W.linear_betas(NT, 2.0, 8.0))
+    J = W.couplings(L, d["j_seed"])
+    eng = pt.Engine(L, np.stack([J] * S), np.stack([betas] * S), n_copies=2, precision=precision, seed=seed)
+    eng.set_params(eps=np.full(S * (NT - 1), d["eps"], np.float32))
+    for _ in range(d["burn"]):
+        eng.sweep(d["n_hb"], d["n_or"])
+        eng.exchange(d["mode"])
+    prop0, acc0 = [a.copy() for a in eng.stats()[:2]]
+    kept = d["cycles"] - d["burn"]
+    H = np.zeros((kept, S, 2, NT))
+    chi = np.zeros((kept, S, NT))
+    for c in range(kept):
+        eng.sweep(d["n_hb"], d["n_or"])
+        eng.exchange(d["mode"])
+        h, q, x = eng.measure()
+        H[c] = h.reshape(S, 2, NT)
+        chi[c] = x.reshape(S, NT)
+    prop, acc = eng.stats()[:2]
+    eng.close()
+    return (H.mean(axis=(0, 2)), chi.mean(axis=0),
+            ((acc - acc0) / np.maximum(prop - prop0, 1)).mean(axis=1))
+
+
+def _z(a, b):
+    ma, ea = a.mean(0), a.std(0, ddof=1) / np.sqrt(a.shape[0])
+    mb, eb = b.mean(0), b.std(0, ddof=1) / np.sqrt(b.shape[0])
+    err = np.sqrt(ea ** 2 + eb ** 2)
+    diff = np.abs(ma - mb)
+    # a pair that no run of either side ever accepted has no spread: equal means pass
+    z = np.where(err > 0, diff / np.where(err > 0, err, 1.0), np.where(diff == 0, 0.0, np.inf))
+    return z, ma, mb, err
+
+
+@pytest.mark.parametrize("L,precision", [(16, "fp32"), (16, "fp64"), (32, "fp32")])
+def test_long_run_parity_at_benchmark_sizes(L, precision):
+    d = _golden(L)
+    g = _gpu_runs(d, precision, S=64, seed=2468 if precision == "fp32" else 1357)
+    o = (np.array(d["H"]), np.array(d["chi"]), np.array(d["acc"]))
+    parts = [_z(a, b) for a, b in zip(g, o)]
+    z = np.concatenate([p[0] for p in parts])
+    msg = "\n".join(f"{n}: z {np.round(p[0], 2)}" for n, p in zip(("H", "chi", "acc"), parts))
+    print(f"\nL={L} {precision}: {len(z)} observables, within 2 sigma {(z < 2).mean():.3f}, max z {z.max():.2f}")
+    assert np.isfinite(z).all(), msg
+    assert (z < 2.0).mean() >= 0.9, msg
+    assert z.max() < 4.0, msg
