@@ -621,11 +621,13 @@ pt_status create_impl(pt_handle* out, int n_samples, const int* Ls, const int* N
     // pair (one configuration each) between its two kernels
     d.heat_buf = nullptr;
     d.heat_H = d.heat_lnJ = nullptr;
+    d.heat_commit = nullptr;
     if (exchange_smem_supported(2, d.max_half, e->fp64) && e->P > 0) {
         const size_t n = (size_t)e->P * 6 * (size_t)d.max_half;
         st = e->dalloc(&d.heat_buf, n * e->esz());
         if (st == PT_OK) st = e->dalloc((void**)&d.heat_H, sizeof(double) * (size_t)e->P);
         if (st == PT_OK) st = e->dalloc((void**)&d.heat_lnJ, sizeof(double) * (size_t)e->P);
+        if (st == PT_OK) st = e->dalloc((void**)&d.heat_commit, sizeof(int) * (size_t)e->P);
         if (st != PT_OK) {
             e->release();
             delete e;

@@ -81,8 +81,6 @@ __device__ void store_chain(const DevBatch& a, const ChainDesc& cd, int NT, Chai
     if (threadIdx.x == 0) a.freebuf[ch] = make_int2(sm.free0, sm.free1);
 }
 
-__device__ __forceinline__ bool metropolis(double lnA, double u) { return lnA >= 0.0 || u < exp(lnA); }
-
 // Sum NV per-thread values over the CTA, then over the cluster in rank order;
 // the totals land in sm.sum[] of every CTA.  Global writes made before the
 // call are visible to the whole cluster after it.  `pub` counts publications
@@ -120,20 +118,20 @@ __device__ __forceinline__ void slice(int n, int rank, int cs, int& lo, int& hi)
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(32) k_exchange_plain(DevBatch a) {
     __shared__ ChainSmem sm;
+    __shared__ PairDraws<MAX_NT> pd;
     const int ch = blockIdx.x;
     const ChainDesc cd = a.chains[ch];
     const SampleDesc& sd = a.samples[cd.s];
     const int NT = sd.NT;
-    load_chain(a, cd, NT, sm, ch);
+    pd.load(a.seed, (uint32_t)cd.s, (uint32_t)cd.copy, *a.d_step, NT - 1);
+    load_chain(a, cd, NT, sm, ch);  // its barrier also publishes pd
     if (threadIdx.x == 0) {
-        const unsigned long long step = *a.d_step;
         const double* beta = a.betas + sd.beta_off;
         for (int i = 0; i + 1 < NT; ++i) {
             const double lnA = (beta[i + 1] - beta[i]) * (sm.H[i + 1] - sm.H[i]);
-            const uint4 w = rng_words(a.seed, (uint32_t)cd.s, (uint32_t)i, (uint32_t)cd.copy, step, 1u);
             a.prop[cd.pair_off + i] += 1;
             xlog_write(a, cd.pair_off + i, lnA, 0.0, 0.0);
-            if (metropolis(lnA, u53(w.x, w.y))) {
+            if (accept_lnu(lnA, pd.lnu[i])) {
                 a.acc[cd.pair_off + i] += 1;
                 int t = sm.buf[i]; sm.buf[i] = sm.buf[i + 1]; sm.buf[i + 1] = t;
                 t = sm.lab[i]; sm.lab[i] = sm.lab[i + 1]; sm.lab[i + 1] = t;
@@ -237,7 +235,7 @@ __device__ __forceinline__ void decimation_chain(const DevBatch& a, cg::cluster_
         if (threadIdx.x == 0) {
             const double lnA = sm.sum[0];
             if (rank == 0) xlog_write(a, cd.pair_off + i, lnA, 0.0, 0.0);
-            const bool ok = metropolis(lnA, pd.u[i]);
+            const bool ok = accept_lnu(lnA, pd.lnu[i]);
             sm.flag = ok;
             if (ok) {
                 pd.acc[i] = 1;
@@ -299,17 +297,18 @@ __device__ __forceinline__ void decimation_chain(const DevBatch& a, cg::cluster_
 template <typename T>
 __global__ void __launch_bounds__(EX_THREADS) k_exchange_coolheat(DevBatch a) {
     __shared__ ChainSmem sm;
+    __shared__ PairDraws<MAX_NT> pd;
     cg::cluster_group cl = cg::this_cluster();
     const int cs = (int)cl.num_blocks(), rank = (int)cl.block_rank();
     const int ch = blockIdx.x / cs;
     const ChainDesc cd = a.chains[ch];
     const SampleDesc& sd = a.samples[cd.s];
     const int NT = sd.NT, half = sd.half;
-    load_chain(a, cd, NT, sm, ch);
+    pd.load(a.seed, (uint32_t)cd.s, (uint32_t)cd.copy, *a.d_step, NT - 1);
+    load_chain(a, cd, NT, sm, ch);  // its barrier also publishes pd
     int lo, hi;
     slice(half, rank, cs, lo, hi);
     int pub = 0;
-    const unsigned long long step = *a.d_step;
     const double* beta = a.betas + sd.beta_off;
     T* pool = (T*)a.spins + a.chain_off[ch];
     const float* J0 = a.J + sd.J_off;
@@ -363,8 +362,7 @@ __global__ void __launch_bounds__(EX_THREADS) k_exchange_coolheat(DevBatch a) {
         if (threadIdx.x == 0) {
             const double LJ1 = sm.sum[0], LJ2 = sm.sum[1], HC = sm.sum[2], HH = sm.sum[3];
             const double lnA = -b2 * HC - b1 * HH + b1 * sm.H[i] + b2 * sm.H[i + 1] + LJ1 - LJ2;
-            const uint4 w = rng_words(a.seed, (uint32_t)cd.s, (uint32_t)i, (uint32_t)cd.copy, step, 1u);
-            const bool ok = metropolis(lnA, u53(w.x, w.y));
+            const bool ok = accept_lnu(lnA, pd.lnu[i]);
             if (rank == 0) {
                 a.prop[cd.pair_off + i] += 1;
                 if (ok) a.acc[cd.pair_off + i] += 1;
@@ -414,7 +412,7 @@ static cudaError_t launch_cluster(K kernel, const DevBatch& b, int cs, cudaStrea
 
 int exchange_launch_count(const DevBatch& b, bool fp64, int mode) {
     // the staged cooling/heating runs the heating pre-pass first
-    if (mode == 2 && b.exchange_impl != 1 && exchange_smem_supported(mode, b.max_half, fp64)) return 2;
+    if (mode == 2 && b.exchange_impl != 1 && exchange_smem_supported(mode, b.max_half, fp64)) return 3;
     return 1;
 }
 

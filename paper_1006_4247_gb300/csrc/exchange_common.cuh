@@ -5,6 +5,9 @@
 
 namespace ptk {
 
+// Metropolis acceptance (section I, Eq. 1) from ln A and ln u.
+__device__ __forceinline__ bool accept_lnu(double lnA, double lnu) { return lnA >= 0.0 || lnu < lnA; }
+
 // Record a pair's log acceptance ratio and, for cooling/heating, its two
 // Jacobian terms (read back by pt_get_exchange_log).
 __device__ __forceinline__ void xlog_write(const DevBatch& a, long long pair, double lnA, double lj1, double lj2) {
@@ -36,18 +39,20 @@ struct DecimPairs {
 
 // The parts of a chain's tempering update that do not depend on the walk's
 // decisions, prepared by the whole block before the walk so that the one
-// thread that decides each pair waits on neither memory nor Philox: the
-// uniform of every pair (purpose 1, c0 = pair, c1 = copy; the same numbers
-// the decision would draw) and a per-pair count of acceptances, added to the
-// global counters once after the walk.
+// thread that decides each pair waits on neither memory, Philox nor a double
+// exponential: ln u of every pair's uniform (purpose 1, c0 = pair, c1 = copy;
+// the same numbers the decision would draw) and a per-pair count of
+// acceptances, added to the global counters once after the walk.  The test
+// u < e^{ln A} is taken as ln u < ln A (the same decision up to the rounding
+// of one logarithm).
 template <int N>
 struct PairDraws {
-    double u[N];
+    double lnu[N];
     int acc[N];
     __device__ void load(uint64_t seed, uint32_t sample, uint32_t copy, unsigned long long step, int n_pairs) {
         for (int i = (int)threadIdx.x; i < n_pairs; i += (int)blockDim.x) {
             const uint4 w = rng_words(seed, sample, (uint32_t)i, copy, step, 1u);
-            u[i] = u53(w.x, w.y);
+            lnu[i] = log(u53(w.x, w.y));  // u = 0 gives -inf: always below ln A
             acc[i] = 0;
         }
     }

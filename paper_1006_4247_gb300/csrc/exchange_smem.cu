@@ -73,8 +73,6 @@ __device__ __forceinline__ void sx_copy(T* __restrict__ dst, const T* __restrict
     }
 }
 
-__device__ __forceinline__ bool sx_metropolis(double lnA, double u) { return lnA >= 0.0 || u < exp(lnA); }
-
 template <typename T>
 __device__ __forceinline__ T sx_decim_D(T n, T b1, T b2, T db, T lr) {
     const T R1 = b1 * n, R2 = b2 * n;
@@ -159,15 +157,32 @@ __global__ void __launch_bounds__(HP_THREADS) k_heat_pre(DevBatch a) {
     }
 }
 
+// Asynchronous 16-byte global -> shared copies (cp.async, cache-global) of n
+// elements by the whole CTA; complete after cp_async_wait_all.
+template <typename T>
+__device__ __forceinline__ void sx_prefetch(T* dst, const T* src, int n) {
+    constexpr int VW = 16 / sizeof(T);
+    for (int q = threadIdx.x * VW; q < n; q += blockDim.x * VW) {
+        const unsigned d = (unsigned)__cvta_generic_to_shared(dst + q);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src + q) : "memory");
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // The pair walk of one chain.  Slot A holds s1 (the configuration now at
 // beta_i), slot F receives f1 = C(s1).  Accept: the heated configuration of
-// beta_{i+1} is final at beta_i and is copied into s1's buffer; f1 moves on
-// as the next s1 (to be written into s2's buffer).  Reject: s1 is final
-// (written back if it was transformed earlier in this update) and s2 is
-// loaded as the next s1.  Buffer identities never change; only contents,
-// labels and energies do.
+// beta_{i+1} is final at beta_i; it belongs in s1's buffer, and the walk
+// only records that (commit[pair] = that buffer; k_heat_commit copies all
+// accepted proposals afterwards, in parallel, since no later pair reads a
+// configuration whose temperature is final); f1 moves on as the next s1 (to
+// be written into s2's buffer).  Reject: s1 is final (written back if it was
+// transformed earlier in this update) and s2 moves on as the next s1.  With
+// room for a third slot G, s2 is fetched into it asynchronously while s1 is
+// cooled, so no pair waits on global memory.  Buffer identities never
+// change; only contents, labels and energies do.
 template <typename T>
-__global__ void __launch_bounds__(SX_THREADS, 1) k_exchange_coolheat_smem(DevBatch a) {
+__global__ void __launch_bounds__(SX_THREADS, 1) k_exchange_coolheat_smem(DevBatch a, int three_slots) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ SxSmem sm;
     __shared__ PairDraws<SX_MAX_NT> pd;
@@ -192,14 +207,14 @@ __global__ void __launch_bounds__(SX_THREADS, 1) k_exchange_coolheat_smem(DevBat
     const float* J0 = a.J + sd.J_off;
     const float* J1 = a.J + sd.J_off + 3 * half;
     const bool v2 = (sd.hL % 2) == 0;
-    int A = 0;               // slot of s1
-    int ownerA = sm.buf[0];  // global buffer of s1
+    int A = 0, F = 1, G = 2;  // slots of s1, of C(s1), of the prefetched s2
+    int ownerA = sm.buf[0];   // global buffer of s1
     bool dirtyA = false;
     sx_copy(slot(A), pool + (long long)ownerA * n3, n3);
     __syncthreads();
     for (int i = 0; i + 1 < NT; ++i) {
-        const int F = 1 - A;
         const int ownerB = sm.buf[i + 1];
+        if (three_slots) sx_prefetch(slot(G), pool + (long long)ownerB * n3, n3);
         const T eps = (T)a.eps[sd.eps_off + i];
         const T* s1 = slot(A);
         T* f1 = slot(F);
@@ -219,8 +234,9 @@ __global__ void __launch_bounds__(SX_THREADS, 1) k_exchange_coolheat_smem(DevBat
             const double b1 = pbeta[i], b2 = pbeta[i + 1];
             const double lnA = -b2 * HC - b1 * HH + b1 * sm.H[i] + b2 * sm.H[i + 1] + LJ1 - LJ2;
             xlog_write(a, pair, lnA, LJ1, LJ2);
-            const bool ok = sx_metropolis(lnA, pd.u[i]);
+            const bool ok = accept_lnu(lnA, pd.lnu[i]);
             sm.flag = ok;
+            a.heat_commit[pair] = ok ? ownerA : -1;
             if (ok) {
                 pd.acc[i] = 1;
                 sm.H[i] = HH;
@@ -230,23 +246,43 @@ __global__ void __launch_bounds__(SX_THREADS, 1) k_exchange_coolheat_smem(DevBat
         }
         __syncthreads();
         if (sm.flag) {
-            // C^-1(s2) is final at beta_i: into s1's buffer; C(s1) moves on
-            sx_copy(pool + (long long)ownerA * n3, (const T*)a.heat_buf + pair * (6LL * a.max_half), n3);
-            A = F;
+            // C^-1(s2) is final at beta_i (committed later); C(s1) moves on
+            const int t = A; A = F; F = t;
             dirtyA = true;
         } else {
             // s1 is final at beta_i; s2 moves on
             if (dirtyA) sx_copy(pool + (long long)ownerA * n3, slot(A), n3);
-            sx_copy(slot(F), pool + (long long)ownerB * n3, n3);
-            A = F;
+            if (three_slots) {
+                const int t = A; A = G; G = t;
+            } else {
+                sx_copy(slot(F), pool + (long long)ownerB * n3, n3);
+                const int t = A; A = F; F = t;
+            }
             dirtyA = false;
         }
         ownerA = ownerB;
+        if (three_slots) cp_async_wait_all();
         __syncthreads();
     }
     if (dirtyA) sx_copy(pool + (long long)ownerA * n3, slot(A), n3);
     sx_store_state(a, cd, NT, sm, ch);
     pd.store(a.prop + cd.pair_off, a.acc + cd.pair_off, NT - 1);
+}
+
+// Accepted heated proposals into the buffers the walk recorded: block
+// (chain, pair), commit[pair] >= 0 names the chain's buffer.
+template <typename T>
+__global__ void __launch_bounds__(HP_THREADS) k_heat_commit(DevBatch a) {
+    const int ch = blockIdx.x, i = blockIdx.y;
+    const ChainDesc cd = a.chains[ch];
+    const SampleDesc& sd = a.samples[cd.s];
+    if (i + 1 >= sd.NT) return;
+    const long long pair = cd.pair_off + i;
+    const int target = a.heat_commit[pair];
+    if (target < 0) return;
+    const int n3 = 6 * sd.half;
+    sx_copy((T*)a.spins + a.chain_off[ch] + (long long)target * n3,
+            (const T*)a.heat_buf + pair * (6LL * a.max_half), n3);
 }
 
 // ---------------------------------------------------------------------------
@@ -303,7 +339,7 @@ __global__ void __launch_bounds__(SX_THREADS, 1) k_exchange_decimation_smem(DevB
         const double lnA = tot1[0];
         if (threadIdx.x == 0) {
             xlog_write(a, cd.pair_off + i, lnA, 0.0, 0.0);
-            const bool ok = sx_metropolis(lnA, pd.u[i]);
+            const bool ok = accept_lnu(lnA, pd.lnu[i]);
             sm.flag = ok;
             if (ok) {
                 pd.acc[i] = 1;
@@ -356,6 +392,12 @@ __global__ void __launch_bounds__(SX_THREADS, 1) k_exchange_decimation_smem(DevB
 // Two slots of one configuration each (s1 and its transform, or the pair).
 size_t exchange_smem_bytes(int mode, int half, bool fp64) { return (size_t)2 * 6 * half * (fp64 ? 8 : 4); }
 
+// A third slot for the cooling/heating walk's prefetch where it fits beside
+// the static tables (about 30 KB) in a CTA's 227 KB.
+static bool coolheat_three_slots(int half, bool fp64) {
+    return (size_t)3 * 6 * half * (fp64 ? 8 : 4) <= 192 * 1024;
+}
+
 bool exchange_smem_supported(int mode, int max_half, bool fp64) {
     // dynamic slots plus about 30 KB of static per-chain tables within the 227 KB of a CTA
     return (mode == 1 || mode == 2) && exchange_smem_bytes(mode, max_half, fp64) <= 196 * 1024;
@@ -367,16 +409,20 @@ cudaError_t launch_exchange_smem(const DevBatch& b, bool fp64, int mode, int max
     if (mode == 2) {
         if (!b.heat_buf) return cudaErrorInvalidValue;  // the engine allocates it whenever this path exists
         const dim3 grid_pre((unsigned)b.n_chains, (unsigned)(b.max_NT - 1), 1);
+        const int three = coolheat_three_slots(max_half, fp64) ? 1 : 0;
+        const size_t smem_w = three ? smem / 2 * 3 : smem;
         if (fp64) {
             k_heat_pre<double><<<grid_pre, HP_THREADS, 0, st>>>(b);
-            e = ensure_smem((const void*)k_exchange_coolheat_smem<double>, smem);
+            e = ensure_smem((const void*)k_exchange_coolheat_smem<double>, smem_w);
             if (e != cudaSuccess) return e;
-            k_exchange_coolheat_smem<double><<<b.n_chains, SX_THREADS, smem, st>>>(b);
+            k_exchange_coolheat_smem<double><<<b.n_chains, SX_THREADS, smem_w, st>>>(b, three);
+            k_heat_commit<double><<<grid_pre, HP_THREADS, 0, st>>>(b);
         } else {
             k_heat_pre<float><<<grid_pre, HP_THREADS, 0, st>>>(b);
-            e = ensure_smem((const void*)k_exchange_coolheat_smem<float>, smem);
+            e = ensure_smem((const void*)k_exchange_coolheat_smem<float>, smem_w);
             if (e != cudaSuccess) return e;
-            k_exchange_coolheat_smem<float><<<b.n_chains, SX_THREADS, smem, st>>>(b);
+            k_exchange_coolheat_smem<float><<<b.n_chains, SX_THREADS, smem_w, st>>>(b, three);
+            k_heat_commit<float><<<grid_pre, HP_THREADS, 0, st>>>(b);
         }
     } else {
         if (fp64) {

@@ -76,6 +76,7 @@ struct DevBatch {
     void* heat_buf;
     double* heat_H;
     double* heat_lnJ;
+    int* heat_commit;  // [pairs] buffer an accepted heated proposal goes to, -1 if rejected
     // [pairs][3]: ln A, ln det J_C(s1), ln det J_C(C^-1 s2) of each pair's
     // most recent proposal (the two Jacobian terms are 0 for the standard
     // and decimation swaps)

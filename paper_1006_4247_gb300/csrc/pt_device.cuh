@@ -316,6 +316,24 @@ template <> struct Rot<double> {
     }
 };
 
+// log(1 + x) in float for the small arguments of ln_jac: with
+// z = x / (2 + x), log(1 + x) = 2 atanh z = 2 (z + z^3/3 + ... + z^9/9), the
+// series cut after z^9 (relative remainder below z^10 / 11: 1e-8 at
+// |x| = 0.5, z = 0.2, and far less at the method's |x| ~ 0.1); the quotient
+// is the hardware one (2 ulp, so a few 1e-7 relative, i.e. ~1e-8 absolute).  Larger |x| (not met while
+// eps |S| is well below 1) take the library log1p.
+__device__ __forceinline__ float log1p_small(float x) {
+    if (fabsf(x) > 0.5f) return log1pf(x);
+    const float z = __fdividef(x, 2.0f + x), z2 = z * z;
+    float t = 1.0f / 9.0f;
+    t = fmaf(t, z2, 1.0f / 7.0f);
+    t = fmaf(t, z2, 0.2f);
+    t = fmaf(t, z2, 1.0f / 3.0f);
+    t = fmaf(t, z2, 1.0f);
+    return 2.0f * z * t;
+}
+__device__ __forceinline__ double log1p_small(double x) { return log1p(x); }
+
 // ln det J_f of one elementary step, ln[(1 - q)(cos a - q sin(a)/a)], with
 // q = eps (S.s) (cooling) or e cos(theta) (heating, at the pre-image).  In
 // float the product is written as 1 + x with x = d - q - q d,
@@ -329,7 +347,7 @@ template <typename T>
 __device__ __forceinline__ T ln_jac(T q, T ca, T cm1, T sc) {
     if (sizeof(T) == 4) {
         const T d = cm1 - q * sc;
-        return M<T>::log1p_(d - q - q * d);
+        return log1p_small(d - q - q * d);
     }
     return M<T>::log_(fabs(((T)1 - q) * (ca - q * sc)));
 }
@@ -356,9 +374,10 @@ __device__ __forceinline__ T cool_site(T eps, const V3<T>& S, V3<T>& s) {
 // Heating step = inverse cooling step: theta' (angle between s' and S) given,
 // find theta with theta - e sin(theta) = theta', e = eps |S| < 1, and rotate
 // s' away from S by alpha = theta - theta'.  The unknown is taken to be alpha
-// itself: alpha = e sin(theta' + alpha), solved by Newton's method from
-// alpha = e sin(theta') with cos(theta') = s'.S/|S| and sin(theta') = |p|/|S|
-// read off the geometry, so no angle is ever formed.  At the solution
+// itself: alpha = e sin(theta' + alpha), solved by Newton's method starting
+// at its first step from 0, e sin(theta') / (1 - e cos(theta')), with
+// cos(theta') = s'.S/|S| and sin(theta') = |p|/|S| read off the geometry, so
+// no angle is ever formed.  At the solution
 // alpha = e sin(theta), hence the Jacobian factors and the rotation reuse
 // sin(alpha), cos(alpha).  Returns ln det J_f at the pre-image,
 // ln[(1 - e cos(theta))(cos(alpha) - e cos(theta) sin(alpha)/alpha)].
@@ -372,7 +391,8 @@ __device__ __forceinline__ T heat_site(T eps, const V3<T>& S, V3<T>& s) {
     const T inv = nS > (T)0 ? MX<T>::div_((T)1, nS) : (T)0;
     const T cp = nS > (T)0 ? sS * inv : (T)1;  // cos(theta')
     const T sp = pn * inv;                     // sin(theta')
-    T alpha = e * sp, cm1, sc;
+    // start from the first Newton step from alpha = 0: e sin(theta') / (1 - e cos(theta'))
+    T alpha = MX<T>::div_(e * sp, (T)1 - e * cp), cm1, sc;
     Rot<T>::cs(alpha, cm1, sc);
     T sa = alpha * sc, ca = (T)1 + cm1;
     for (int it = 0; it < M<T>::newton_max; ++it) {

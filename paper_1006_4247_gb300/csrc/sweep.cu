@@ -21,7 +21,7 @@ namespace ptk {
 // Tiles: tile_begin + blockIdx.x indexes `tidx` (the streaming subset) when
 // it is given, else vtiles directly.
 template <typename T, int V, int KIND, bool ENERGY>
-__global__ void __launch_bounds__(TILE) k_sweep(DevBatch a, const int* __restrict__ tidx, int tile_begin,
+__global__ void __launch_bounds__(TILE, KIND == 1 ? 5 : 6) k_sweep(DevBatch a, const int* __restrict__ tidx, int tile_begin,
                                                 int color, int step_k, int or_index) {
     __shared__ double sh[32];
     const int t = tidx ? tidx[tile_begin + (int)blockIdx.x] : tile_begin + (int)blockIdx.x;
