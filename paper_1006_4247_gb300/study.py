@@ -272,6 +272,44 @@ def learned_large(L=48, n_samples=32, n_run=8, cycles=300, burn=200, kappa=0.1, 
                         "acc_mean": float(acc_l.mean()), "acc_profile": acc_l.mean(0).round(4).tolist()}}
 
 
+def learned_large_roundtrip(L=48, n_run=8, cycles=3000, burn=1500, kappa=0.1, seed0=400, reduce=0.85):
+    """Round trips at a size outside the network's training range (L = 48,
+    coupling seeds 400 + k, the first n_run sets): the geometric ladder with
+    one kappa and the learned ladder with its per-pair epsilon, each at the
+    paper's replica rule N_T and at round(reduce * N_T) replicas, after a
+    burn-in from a random start.  Reported per arm: t_R (sweeps of the
+    measured cycles over the round trips of all 2 N_T configurations, mean
+    and standard error over the sets), the median tau_int(chi) at the lowest
+    temperature in sweeps, and the acceptance (worst pair, mean)."""
+    J = [workloads.couplings(L, seed0 + k) for k in range(n_run)]
+    bmin, bmax = 1 / T_MAX, 1 / T_MIN
+    spc = 1 + max(1, (5 * L) // 4)
+    nt_full = ladder.default_n_temps(L, bmin, bmax)
+    nt_red = int(round(reduce * nt_full))
+    bound = min(ladder.eps_bound(L, j) for j in J)
+    out = {"L": L, "sets": n_run, "cycles": cycles, "burn": burn, "sweeps_per_cycle": spc, "kappa": kappa,
+           "n_temps": [nt_full, nt_red], "arms": {}}
+    for nt in (nt_full, nt_red):
+        geo = paper_ladder(nt)
+        net = ladder.LearnedLadder.load()
+        try:
+            prop = net.propose_many([(L, j, bmin, bmax) for j in J], n_temps=nt)
+        finally:
+            net.close()
+        arms = {"geometric": (geo, ladder.eps_from_kappa(geo, np.full(nt - 1, kappa), bound)),
+                "learned": (np.stack([b for b, _ in prop]), np.stack([e for _, e in prop]))}
+        for name, (betas, eps) in arms.items():
+            acc, rt, chi = run_method(L, J, betas, "coolheat", eps, cycles, burn, seed=19)
+            tR = cycles * spc / np.maximum(rt, 1)
+            tau = [tau_int(chi[:, k]) * spc for k in range(n_run)]
+            out["arms"][f"{name}_{nt}"] = {
+                "n_temps": nt, "t_R": float(tR.mean()), "t_R_se": float(tR.std(ddof=1) / math.sqrt(n_run)),
+                "round_trips_per_set": rt.tolist(), "tau_int_median": float(np.nanmedian(tau)),
+                "acc_min": float(acc.min(1).mean()), "acc_mean": float(acc.mean()),
+                "acc_profile": acc.mean(0).round(4).tolist()}
+    return out
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description="the paper's protocol on synthetic coupling sets")
     ap.add_argument("--L", type=int, default=16)
@@ -286,10 +324,15 @@ def main(argv=None):
                     help="replica study: the standard swap at the paper's N_T only")
     ap.add_argument("--equilibration", type=int, default=0, help="runs of the equilibration study (0: off)")
     ap.add_argument("--learned-large", action="store_true", help="learned ladder at L (e.g. 48) vs geometric")
+    ap.add_argument("--learned-large-rt", action="store_true",
+                    help="round trips of the learned and the geometric ladder at L (e.g. 48), full and reduced N_T")
+    ap.add_argument("--run-sets", type=int, default=8, help="--learned-large-rt: coupling sets run")
     ap.add_argument("--log", default="", help="also append the result as a JSON-lines run record to this file")
     a = ap.parse_args(argv)
     nt = a.n_temps or {16: 15, 24: 27, 32: 43}.get(a.L, ladder.default_n_temps(a.L, 1 / T_MAX, 1 / T_MIN))
-    if a.learned_large:
+    if a.learned_large_rt:
+        kind, out = "learned_large_rt", learned_large_roundtrip(a.L, a.run_sets, a.cycles, a.burn, a.kappa)
+    elif a.learned_large:
         kind, out = "learned_large", learned_large(a.L, cycles=a.cycles, burn=a.burn)
     elif a.equilibration:
         kind, out = "equilibration", equilibration(a.L, nt, a.equilibration, a.cycles, a.kappa)
