@@ -107,7 +107,11 @@ template <> struct M<float> {
     static __device__ __forceinline__ float copysign_(float a, float b) { return copysignf(a, b); }
     static constexpr float tinyR = 1e-30f;
     static constexpr int newton_max = 30;
-    static constexpr float newton_tol = 2e-7f;
+    // heating step: after a Newton step of size d the root is within
+    // e / (2 (1 - e)) d^2 (f'' = e sin, f' >= 1 - e), so stopping at
+    // |d| < 1e-4 leaves < 5e-8 rad even at e = 0.9 (the float ulp of an angle
+    // ~1 is 6e-8), one iteration earlier than |d| < 2e-7
+    static constexpr float newton_tol = 1e-4f;
     static constexpr float pi = CUDART_PI_F;
 };
 template <> struct M<double> {
@@ -291,8 +295,9 @@ __device__ __forceinline__ T ln_sinhc(T R) {
 // relative, error.  Double uses the library functions.
 template <typename T> struct Rot;
 template <> struct Rot<float> {
-    static __device__ __forceinline__ void cs(float a, float& cm1, float& sc) {
-        const float a2 = a * a;
+    static __device__ __forceinline__ void cs(float a, float& cm1, float& sc) { cs2(a * a, cm1, sc); }
+    // from a^2 (both series are even): the cooling step needs no square root
+    static __device__ __forceinline__ void cs2(float a2, float& cm1, float& sc) {
         // cos a - 1 = -a^2/2! + a^4/4! - a^6/6! + a^8/8! - a^10/10!
         float c = -2.7557319e-7f;
         c = fmaf(c, a2, 2.4801587e-5f);
@@ -314,6 +319,7 @@ template <> struct Rot<double> {
         cm1 = cos(a) - 1.0;
         sc = a == 0.0 ? 1.0 : sin(a) / a;
     }
+    static __device__ __forceinline__ void cs2(double a2, double& cm1, double& sc) { cs(sqrt(a2), cm1, sc); }
 };
 
 // log(1 + x) in float for the small arguments of ln_jac: with
@@ -358,10 +364,9 @@ template <typename T>
 __device__ __forceinline__ T cool_site(T eps, const V3<T>& S, V3<T>& s) {
     const T sS = dot(s, S);
     const V3<T> p = {S.x - sS * s.x, S.y - sS * s.y, S.z - sS * s.z};
-    const T pn = M<T>::sqrt_(dot(p, p));
-    const T alpha = eps * pn;
+    // alpha = eps |p| enters only through its square
     T cm1, sc;
-    Rot<T>::cs(alpha, cm1, sc);
+    Rot<T>::cs2(eps * eps * dot(p, p), cm1, sc);
     const T ca = (T)1 + cm1;
     const T f = eps * sc;
     s.x = s.x * ca + p.x * f;
