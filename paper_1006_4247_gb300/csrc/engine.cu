@@ -618,7 +618,8 @@ pt_status create_impl(pt_handle* out, int n_samples, const int* Ls, const int* N
     d.max_half = 0;
     for (const SampleDesc& sd : e->samples) d.max_half = std::max(d.max_half, sd.half);
     // the staged cooling/heating exchange keeps the heated proposal of every
-    // pair (one configuration each) between its two kernels
+    // pair (one configuration each) from the heating pre-pass through the walk
+    // to the commit of the accepted ones
     d.heat_buf = nullptr;
     d.heat_H = d.heat_lnJ = nullptr;
     d.heat_commit = nullptr;

@@ -411,7 +411,7 @@ static cudaError_t launch_cluster(K kernel, const DevBatch& b, int cs, cudaStrea
 }
 
 int exchange_launch_count(const DevBatch& b, bool fp64, int mode) {
-    // the staged cooling/heating runs the heating pre-pass first
+    // the staged cooling/heating: heating pre-pass, walk, commit of the accepted proposals
     if (mode == 2 && b.exchange_impl != 1 && exchange_smem_supported(mode, b.max_half, fp64)) return 3;
     return 1;
 }
