@@ -13,6 +13,9 @@ at the sizes of the benchmark batches (calls only the oracle).
           inverse temperatures linear in [2.0, 8.0], two copies, 1 + 40 sweeps
           and one decimation update per cycle; 40 cycles of which the first 10
           are discarded; 24 independent runs (seeds 9200..9223).
+  L = 16 with the standard swap (stats_L16_R24_plain.json, seeds 9300..9331)
+          and with decimation (stats_L16_R24_decimation.json, seeds
+          9400..9431), otherwise as the first case.
 
 Every run starts from spins uniform on the sphere (its own Philox stream), so
 the per-run averages are independent draws of the same random variable for
@@ -20,7 +23,7 @@ the oracle and for the engine, whether or not the chains have reached
 equilibrium by then.  Runs are spread over the host's cores (one process per
 run, started with spawn); about 4 min (L = 16) and 20 min (L = 32) on 8 cores.
 
-    python tests/golden/make_stats_large.py [16] [32]
+    python tests/golden/make_stats_large.py [16] [32] [161] [162]
 """
 import json
 import multiprocessing as mp
@@ -38,14 +41,20 @@ CASES = {
          "mode": ("coolheat", 2, float(np.float32(0.017))), "cycles": 150, "burn": 50, "runs": 32, "seed0": 9100},
     32: {"file": "stats_L32_R48.json", "NT": 48, "j_seed": 200, "n_or": 40, "mode": ("decimation", 1, 0.0),
          "cycles": 40, "burn": 10, "runs": 24, "seed0": 9200},
+    # configuration 2's other exchanges: the standard swap and decimation
+    161: {"L": 16, "file": "stats_L16_R24_plain.json", "NT": 24, "j_seed": 100, "n_or": 20,
+          "mode": ("plain", 0, 0.0), "cycles": 150, "burn": 50, "runs": 32, "seed0": 9300},
+    162: {"L": 16, "file": "stats_L16_R24_decimation.json", "NT": 24, "j_seed": 100, "n_or": 20,
+          "mode": ("decimation", 1, 0.0), "cycles": 150, "burn": 50, "runs": 32, "seed0": 9400},
 }
 
 
 def one_run(job):
-    L, r = job
+    key, r = job
     import oracle as orc
     from paper_1006_4247_gb300 import workloads as W
-    c = CASES[L]
+    c = CASES[key]
+    L = c.get("L", key)
     betas = W.linear_betas(c["NT"], 2.0, 8.0)
     J = W.couplings(L, c["j_seed"]).astype(np.float64)
     name, mode, eps = c["mode"]
@@ -63,11 +72,12 @@ def main(sizes):
     import oracle as orc
     orc.build()
     ctx = mp.get_context("spawn")
-    for L in sizes:
-        c = CASES[L]
+    for key in sizes:
+        c = CASES[key]
+        L = c.get("L", key)
         t0 = time.time()
         with ctx.Pool(os.cpu_count() or 1) as pool:
-            res = pool.map(one_run, [(L, r) for r in range(c["runs"])])
+            res = pool.map(one_run, [(key, r) for r in range(c["runs"])])
         from paper_1006_4247_gb300 import workloads as W
         name, mode, eps = c["mode"]
         out = {"L": L, "NT": c["NT"], "j_seed": c["j_seed"], "n_hb": 1, "n_or": c["n_or"], "cycles": c["cycles"],
@@ -80,4 +90,4 @@ def main(sizes):
 
 
 if __name__ == "__main__":
-    main([int(a) for a in sys.argv[1:]] or [16, 32])
+    main([int(a) for a in sys.argv[1:]] or list(CASES))

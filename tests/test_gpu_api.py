@@ -75,6 +75,28 @@ def test_set_spins_normalises_and_rejects_zero(precision):
     eng.close()
 
 
+def test_exchange_log_and_smem_probe():
+    """pt_get_exchange_log is zero before the first tempering update and holds
+    every pair's ln A afterwards (the standard swap: (b2 - b1)(H2 - H1) of the
+    energies before the update, no Jacobian terms); pt_smem_bandwidth reports
+    a rate between 10 and 100 TB/s (GB300: about 40), up to 256 B per clock per
+    SM, and the clock it ran at."""
+    eng, J, B = make_engine(8, 2, 4, 2, "fp32")
+    lnA, lnJ = eng.exchange_log()
+    assert lnA.shape == (2, 2, 3) and lnJ.shape == (2, 2, 3, 2)
+    assert (lnA == 0).all() and (lnJ == 0).all()
+    H0 = eng.energies()
+    eng.exchange("plain")
+    lnA, lnJ = eng.exchange_log()
+    assert (lnJ == 0).all()
+    # pair 0 of each chain sees the energies before the update
+    ref = (B[:, 1] - B[:, 0])[:, None] * (H0[:, :, 1] - H0[:, :, 0])
+    assert np.allclose(lnA[:, :, 0], ref, rtol=1e-12, atol=1e-12)
+    eng.close()
+    bps, bpc, mhz = pt.pt_smem_bandwidth()
+    assert 10e12 < bps < 100e12 and 0 < bpc <= 256 and 500 < mhz < 3000, (bps, bpc, mhz)
+
+
 def test_error_statuses():
     eng, J, B = make_engine(4, 1, 3, 2, "fp32")
     with pytest.raises(pt.PtError) as ei:

@@ -6,7 +6,9 @@ the overlap susceptibility, errors from independent runs).
   overrelaxation sweeps and one cooling/heating update (eps = 0.017) per
   cycle, 150 cycles with the first 50 discarded (the configuration-2 batch);
   L = 32, 48 inverse temperatures, 1 + 40 sweeps and one decimation update,
-  40 cycles with the first 10 discarded (the configuration-3 batch).
+  40 cycles with the first 10 discarded (the configuration-3 batch);
+  L = 16 as the first case with the standard swap and with decimation
+  (configuration 2 compares the standard swap with the modified exchanges).
 
 Both sides run independent chain pairs of one coupling set from spins uniform
 on the sphere: the oracle's per-run averages are stored in tests/golden/ by
@@ -30,7 +32,8 @@ from paper_1006_4247_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-GOLDEN = {16: "stats_L16_R24.json", 32: "stats_L32_R48.json"}
+CASES = [("stats_L16_R24.json", "fp32"), ("stats_L16_R24.json", "fp64"), ("stats_L32_R48.json", "fp32"),
+         ("stats_L16_R24_plain.json", "fp32"), ("stats_L16_R24_decimation.json", "fp32")]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -39,8 +42,8 @@ def _built():
     _build.build()
 
 
-def _golden(L):
-    with open(os.path.join(HERE, "golden", GOLDEN[L])) as fh:
+def _golden(name):
+    with open(os.path.join(HERE, "golden", name)) as fh:
         return json.load(fh)
 
 
@@ -80,15 +83,17 @@ def _z(a, b):
     return z, ma, mb, err
 
 
-@pytest.mark.parametrize("L,precision", [(16, "fp32"), (16, "fp64"), (32, "fp32")])
-def test_long_run_parity_at_benchmark_sizes(L, precision):
-    d = _golden(L)
+@pytest.mark.parametrize("golden,precision", CASES)
+def test_long_run_parity_at_benchmark_sizes(golden, precision):
+    d = _golden(golden)
+    L = d["L"]
     g = _gpu_runs(d, precision, S=64, seed=2468 if precision == "fp32" else 1357)
     o = (np.array(d["H"]), np.array(d["chi"]), np.array(d["acc"]))
     parts = [_z(a, b) for a, b in zip(g, o)]
     z = np.concatenate([p[0] for p in parts])
     msg = "\n".join(f"{n}: z {np.round(p[0], 2)}" for n, p in zip(("H", "chi", "acc"), parts))
-    print(f"\nL={L} {precision}: {len(z)} observables, within 2 sigma {(z < 2).mean():.3f}, max z {z.max():.2f}")
+    print(f"\nL={L} {d['mode']} {precision}: {len(z)} observables, within 2 sigma {(z < 2).mean():.3f}, "
+          f"max z {z.max():.2f}")
     assert np.isfinite(z).all(), msg
     assert (z < 2.0).mean() >= 0.9, msg
     assert z.max() < 4.0, msg
