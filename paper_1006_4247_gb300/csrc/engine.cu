@@ -587,6 +587,8 @@ pt_status create_impl(pt_handle* out, int n_samples, const int* Ls, const int* N
     TRY(upload(e, &d.chi, zx));
     std::vector<double> zl((size_t)pair * 3, 0.0);
     TRY(upload(e, &d.xlog, zl));
+    std::vector<double> zd((size_t)pair * 2, 0.0);
+    TRY(upload(e, &d.decim_pre, zd));
 #undef TRY
     d.seed = e->seed;
     d.n_samples = e->S;

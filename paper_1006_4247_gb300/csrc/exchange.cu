@@ -27,6 +27,7 @@ namespace ptk {
 
 constexpr int MAX_NT = 512;
 constexpr int EX_THREADS = 512;
+constexpr int HPX_THREADS = 256;  // k_decim_pre
 constexpr int MAX_SUMS = 4;
 
 struct ChainSmem {
@@ -193,8 +194,78 @@ __global__ void __launch_bounds__(EX_THREADS, 2) k_exchange_decimation(DevBatch 
     cl.sync();  // no CTA leaves while others may still read its shared memory
 }
 
+// Sum over the V-site vectors [lo, hi) of colour d (this thread's share) of
+// D(|S|) = ln I(b2 |S|) - ln I(b1 |S|), S the field of config c's other colour.
+template <typename T, int V>
+__device__ __forceinline__ T decim_sum(const SampleDesc& sd, const T* c, const float* Jd, const float* Jk, int d,
+                                       int lo, int hi, int tid, int nth, T b1t, T b2t, T dbt, T lr) {
+    const int half = sd.half;
+    T part = (T)0;
+    for (int h0 = lo + tid * V; h0 < hi; h0 += nth * V) {
+        const VRow q = vrow<V>(sd, d, h0);
+        T S[3][V];
+        nbr_field<T, V>(c + (1 - d) * 3 * half, Jd, Jk, half, h0, q.xs, q.hyp, q.hym, q.hzp, q.hzm, q.p, S);
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const T n = M<T>::sqrt_(S[0][v] * S[0][v] + S[1][v] * S[1][v] + S[2][v] * S[2][v]);
+            part += decim_D<T>(n, b1t, b2t, dbt, lr);
+        }
+    }
+    return part;
+}
+
+// The two halves of every pair's ln A that do not depend on the walk:
+// T1 = sum over the decimated colour d_i of D(|S|) for the configuration at
+// beta_i as the update found it, T2 the same for the one at beta_{i+1}
+// (ln A = T1 - T2 when pair i-1 left beta_i's configuration alone, which
+// pair i-1 does unless it accepted).  Block (chain, pair); stored in
+// decim_pre[2 pair], [2 pair + 1].
+template <typename T>
+__global__ void __launch_bounds__(HPX_THREADS) k_decim_pre(DevBatch a) {
+    __shared__ double red[2 * 32];
+    const int ch = blockIdx.x, i = blockIdx.y;
+    const ChainDesc cd = a.chains[ch];
+    const SampleDesc& sd = a.samples[cd.s];
+    if (i + 1 >= sd.NT) return;  // uniform over the block
+    const int half = sd.half, n3 = 6 * half;
+    const uint4 wd = rng_words(a.seed, (uint32_t)cd.s, 0u, (uint32_t)cd.copy, *a.d_step, 3u);
+    const int d = (int)((wd.x & 1u) + (uint32_t)i) & 1;
+    const T* pool = (const T*)a.spins + a.chain_off[ch];
+    const T* c1 = pool + (long long)a.bufmap[cd.r0 + i] * n3;
+    const T* c2 = pool + (long long)a.bufmap[cd.r0 + i + 1] * n3;
+    const float* Jd = a.J + sd.J_off + d * 3 * half;
+    const float* Jk = a.J + sd.J_off + (1 - d) * 3 * half;
+    // the walk's per-pair constants (DecimPairs), for this pair only
+    const double b1 = a.betas[sd.beta_off + i], b2 = a.betas[sd.beta_off + i + 1];
+    const T b1t = (T)b1, b2t = (T)b2, dbt = (T)(b2 - b1), lr = b1 > 0.0 ? (T)log(b2 / b1) : (T)0;
+    T part[2];
+    const int tid = (int)threadIdx.x, nth = (int)blockDim.x;
+    constexpr int V4 = sizeof(T) == 4 ? 4 : 2;  // 16-byte rows
+    if (sd.vec == 4) {
+        part[0] = decim_sum<T, V4>(sd, c1, Jd, Jk, d, 0, half, tid, nth, b1t, b2t, dbt, lr);
+        part[1] = decim_sum<T, V4>(sd, c2, Jd, Jk, d, 0, half, tid, nth, b1t, b2t, dbt, lr);
+    } else if (sd.vec >= 2) {
+        part[0] = decim_sum<T, 2>(sd, c1, Jd, Jk, d, 0, half, tid, nth, b1t, b2t, dbt, lr);
+        part[1] = decim_sum<T, 2>(sd, c2, Jd, Jk, d, 0, half, tid, nth, b1t, b2t, dbt, lr);
+    } else {
+        part[0] = decim_sum<T, 1>(sd, c1, Jd, Jk, d, 0, half, tid, nth, b1t, b2t, dbt, lr);
+        part[1] = decim_sum<T, 1>(sd, c2, Jd, Jk, d, 0, half, tid, nth, b1t, b2t, dbt, lr);
+    }
+    double tot[2];
+    block_sum_exact<T, 2>(part, tot, red);
+    if (threadIdx.x == 0) {
+        a.decim_pre[2 * (cd.pair_off + i)] = tot[0];
+        a.decim_pre[2 * (cd.pair_off + i) + 1] = tot[1];
+    }
+}
+
 // The pair walk of one chain; this CTA handles its slice of the V-site
-// vectors of the decimated colour (16-byte loads of the neighbour rows).
+// vectors (16-byte loads of the neighbour rows).  ln A of pair i is
+// T1 - T2 (k_decim_pre) unless pair i-1 accepted: then the configuration now
+// at beta_i is the one re-inserted at the end of pair i-1, whose kept colour
+// (d_{i-1}) changed, and its T1 is summed right after the re-insertion.  A
+// rejected pair therefore needs no lattice work and no cluster-wide step: all
+// CTAs read the same T1, T2 and take the same decision.
 template <typename T, int V>
 __device__ __forceinline__ void decimation_chain(const DevBatch& a, cg::cluster_group& cl, ChainSmem& sm,
                                                  const DecimPairs<T, MAX_NT>& dp, PairDraws<MAX_NT>& pd,
@@ -208,32 +279,18 @@ __device__ __forceinline__ void decimation_chain(const DevBatch& a, cg::cluster_
     int pub = 0;
     const unsigned long long step = *a.d_step;
     T* pool = (T*)a.spins + a.chain_off[ch];
+    const double* pre = a.decim_pre + 2LL * cd.pair_off;
     const uint4 wd = rng_words(a.seed, (uint32_t)cd.s, 0u, (uint32_t)cd.copy, step, 3u);
     const int d0 = (int)(wd.x & 1u);
+    bool fresh = true;  // the configuration at beta_i is the one the update started with
+    double T1cur = 0.0;
     for (int i = 0; i + 1 < NT; ++i) {
         const int d = (d0 + i) & 1;
         const T b1t = dp.b[i], b2t = dp.b[i + 1];
-        const T* c1 = pool + (long long)sm.buf[i] * (6LL * half);
-        const T* c2 = pool + (long long)sm.buf[i + 1] * (6LL * half);
         const float* Jd = a.J + sd.J_off + d * 3 * half;
         const float* Jk = a.J + sd.J_off + (1 - d) * 3 * half;
-        const T dbt = dp.db[i], lr = dp.lr[i];
-        T part[1] = {(T)0};
-        for (int h0 = lo + (int)threadIdx.x * V; h0 < hi; h0 += (int)blockDim.x * V) {
-            const VRow q = vrow<V>(sd, d, h0);
-            T S1[3][V], S2[3][V];
-            nbr_field<T, V>(c1 + (1 - d) * 3 * half, Jd, Jk, half, h0, q.xs, q.hyp, q.hym, q.hzp, q.hzm, q.p, S1);
-            nbr_field<T, V>(c2 + (1 - d) * 3 * half, Jd, Jk, half, h0, q.xs, q.hyp, q.hym, q.hzp, q.hzm, q.p, S2);
-#pragma unroll
-            for (int v = 0; v < V; ++v) {
-                const T na = M<T>::sqrt_(S1[0][v] * S1[0][v] + S1[1][v] * S1[1][v] + S1[2][v] * S1[2][v]);
-                const T nb = M<T>::sqrt_(S2[0][v] * S2[0][v] + S2[1][v] * S2[1][v] + S2[2][v] * S2[2][v]);
-                part[0] += decim_D<T>(na, b1t, b2t, dbt, lr) - decim_D<T>(nb, b1t, b2t, dbt, lr);
-            }
-        }
-        cluster_sum<T, 1>(cl, sm, part, pub);
         if (threadIdx.x == 0) {
-            const double lnA = sm.sum[0];
+            const double lnA = (fresh ? pre[2 * i] : T1cur) - pre[2 * i + 1];
             if (rank == 0) xlog_write(a, cd.pair_off + i, lnA, 0.0, 0.0);
             const bool ok = accept_lnu(lnA, pd.lnu[i]);
             sm.flag = ok;
@@ -244,6 +301,7 @@ __device__ __forceinline__ void decimation_chain(const DevBatch& a, cg::cluster_
             }
         }
         __syncthreads();
+        fresh = !sm.flag;
         if (sm.flag) {
             T e[2] = {(T)0, (T)0};
             T* n1 = pool + (long long)sm.buf[i] * (6LL * half);      // now at b1
@@ -273,10 +331,20 @@ __device__ __forceinline__ void decimation_chain(const DevBatch& a, cg::cluster_
                     for (int c = 0; c < 3; ++c) stv<T, V>(nb_ + d * 3 * half + c * half + h0, out[c]);
                 }
             }
-            cluster_sum<T, 2>(cl, sm, e, pub);
+            cluster_sum<T, 2>(cl, sm, e, pub);  // also makes the re-inserted spins visible to the cluster
             if (threadIdx.x == 0) {
                 sm.H[i] = sm.sum[0];
                 sm.H[i + 1] = sm.sum[1];
+            }
+            if (i + 2 < NT) {
+                // T1 of pair i+1: its decimated colour is 1 - d, the kept colour d was just redrawn
+                const int dn = 1 - d;
+                const float* Jdn = a.J + sd.J_off + dn * 3 * half;
+                const float* Jkn = a.J + sd.J_off + d * 3 * half;
+                T part[1] = {decim_sum<T, V>(sd, n2, Jdn, Jkn, dn, lo, hi, (int)threadIdx.x, (int)blockDim.x,
+                                             dp.b[i + 1], dp.b[i + 2], dp.db[i + 1], dp.lr[i + 1])};
+                cluster_sum<T, 1>(cl, sm, part, pub);
+                T1cur = sm.sum[0];
             }
             __syncthreads();
         }
@@ -413,6 +481,8 @@ static cudaError_t launch_cluster(K kernel, const DevBatch& b, int cs, cudaStrea
 int exchange_launch_count(const DevBatch& b, bool fp64, int mode) {
     // the staged cooling/heating: heating pre-pass, walk, commit of the accepted proposals
     if (mode == 2 && b.exchange_impl != 1 && exchange_smem_supported(mode, b.max_half, fp64)) return 3;
+    // the cluster decimation walk runs after the pre-pass of its sums
+    if (mode == 1 && !(b.exchange_impl != 1 && exchange_smem_supported(mode, b.max_half, fp64))) return 2;
     return 1;
 }
 
@@ -425,9 +495,15 @@ cudaError_t launch_exchange(const DevBatch& b, bool fp64, int mode, cudaStream_t
         return launch_exchange_smem(b, fp64, mode, b.max_half, st);
     const int cs = b.exchange_cluster > 0 ? b.exchange_cluster : cluster_size(b);
     cudaError_t e;
-    if (mode == 1)
+    if (mode == 1) {
+        const dim3 grid_pairs((unsigned)b.n_chains, (unsigned)(b.max_NT - 1), 1);
+        if (fp64) k_decim_pre<double><<<grid_pairs, HPX_THREADS, 0, st>>>(b);
+        else k_decim_pre<float><<<grid_pairs, HPX_THREADS, 0, st>>>(b);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
         e = fp64 ? launch_cluster(k_exchange_decimation<double>, b, cs, st)
                  : launch_cluster(k_exchange_decimation<float>, b, cs, st);
+    }
     else
         e = fp64 ? launch_cluster(k_exchange_coolheat<double>, b, cs, st)
                  : launch_cluster(k_exchange_coolheat<float>, b, cs, st);

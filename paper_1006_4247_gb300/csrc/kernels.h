@@ -77,6 +77,9 @@ struct DevBatch {
     double* heat_H;
     double* heat_lnJ;
     int* heat_commit;  // [pairs] buffer an accepted heated proposal goes to, -1 if rejected
+    // [pairs][2] the decimation sums T1, T2 of every pair over the
+    // configurations as the update found them (cluster decimation walk)
+    double* decim_pre;
     // [pairs][3]: ln A, ln det J_C(s1), ln det J_C(C^-1 s2) of each pair's
     // most recent proposal (the two Jacobian terms are 0 for the standard
     // and decimation swaps)
