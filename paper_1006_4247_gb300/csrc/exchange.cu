@@ -38,7 +38,7 @@ struct ChainSmem {
     double red[MAX_SUMS * 32];
     double slot[2][MAX_SUMS];  // published partials (double-buffered)
     double sum[MAX_SUMS];      // cluster totals, in rank order
-    int flag;
+    int flag2[2];              // decision of pair i in flag2[i & 1] (the decimation walk)
     int free0, free1;
 };
 
@@ -293,7 +293,9 @@ __device__ __forceinline__ void decimation_chain(const DevBatch& a, cg::cluster_
             const double lnA = (fresh ? pre[2 * i] : T1cur) - pre[2 * i + 1];
             if (rank == 0) xlog_write(a, cd.pair_off + i, lnA, 0.0, 0.0);
             const bool ok = accept_lnu(lnA, pd.lnu[i]);
-            sm.flag = ok;
+            // by pair parity: after a rejection no barrier separates this
+            // write from other warps' read of the previous pair's decision
+            sm.flag2[i & 1] = ok;
             if (ok) {
                 pd.acc[i] = 1;
                 int t = sm.buf[i]; sm.buf[i] = sm.buf[i + 1]; sm.buf[i + 1] = t;
@@ -301,8 +303,9 @@ __device__ __forceinline__ void decimation_chain(const DevBatch& a, cg::cluster_
             }
         }
         __syncthreads();
-        fresh = !sm.flag;
-        if (sm.flag) {
+        const bool accepted = sm.flag2[i & 1] != 0;
+        fresh = !accepted;
+        if (accepted) {
             T e[2] = {(T)0, (T)0};
             T* n1 = pool + (long long)sm.buf[i] * (6LL * half);      // now at b1
             T* n2 = pool + (long long)sm.buf[i + 1] * (6LL * half);  // now at b2
