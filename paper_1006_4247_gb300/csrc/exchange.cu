@@ -235,9 +235,19 @@ __global__ void __launch_bounds__(HPX_THREADS) k_decim_pre(DevBatch a) {
     const T* c2 = pool + (long long)a.bufmap[cd.r0 + i + 1] * n3;
     const float* Jd = a.J + sd.J_off + d * 3 * half;
     const float* Jk = a.J + sd.J_off + (1 - d) * 3 * half;
-    // the walk's per-pair constants (DecimPairs), for this pair only
-    const double b1 = a.betas[sd.beta_off + i], b2 = a.betas[sd.beta_off + i + 1];
-    const T b1t = (T)b1, b2t = (T)b2, dbt = (T)(b2 - b1), lr = b1 > 0.0 ? (T)log(b2 / b1) : (T)0;
+    // the walk's per-pair constants (DecimPairs), for this pair only, formed
+    // in double by lane 0 of each warp and broadcast
+    T k4[4] = {(T)0, (T)0, (T)0, (T)0};
+    if ((threadIdx.x & 31u) == 0u) {
+        const double b1 = a.betas[sd.beta_off + i], b2 = a.betas[sd.beta_off + i + 1];
+        k4[0] = (T)b1;
+        k4[1] = (T)b2;
+        k4[2] = (T)(b2 - b1);
+        k4[3] = b1 > 0.0 ? (T)log(b2 / b1) : (T)0;
+    }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) k4[m] = __shfl_sync(0xFFFFFFFFu, k4[m], 0);
+    const T b1t = k4[0], b2t = k4[1], dbt = k4[2], lr = k4[3];
     T part[2];
     const int tid = (int)threadIdx.x, nth = (int)blockDim.x;
     constexpr int V4 = sizeof(T) == 4 ? 4 : 2;  // 16-byte rows

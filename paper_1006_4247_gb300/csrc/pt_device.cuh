@@ -132,14 +132,35 @@ template <> struct M<double> {
     static constexpr double pi = CUDART_PI;
 };
 
-// Quotients of the cooling / heating transforms.  Float uses the hardware
-// reciprocal quotient (2 ulp; operands O(1) or small angles); double divides.
+// Quotients, square roots and the azimuth of the heat bath, cooling and
+// heating steps.  Float takes the hardware forms: the reciprocal quotient
+// (2 ulp; every divisor is O(1), an angle, or |S| of a site), the reciprocal
+// square root (2 ulp), and sin/cos of pi x, whose argument reduction is exact
+// (the azimuth is 2 pi u with u on a 2^-24 grid, so 2u is exact).  Double
+// divides, takes the square root and the sine and cosine of 2 pi u.
 template <typename T> struct MX;
 template <> struct MX<float> {
     static __device__ __forceinline__ float div_(float a, float b) { return __fdividef(a, b); }
+    // |S| and 1 / |S| from |S|^2 > 0
+    static __device__ __forceinline__ void len_inv_(float x, float& n, float& inv) {
+        inv = rsqrtf(x);
+        n = x * inv;
+    }
+    // sqrt(x), x >= 0
+    static __device__ __forceinline__ float sqrt0_(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
+    // sin and cos of 2 pi u
+    static __device__ __forceinline__ void sincos_turn_(float u, float* s, float* c) { sincospif(2.0f * u, s, c); }
 };
 template <> struct MX<double> {
     static __device__ __forceinline__ double div_(double a, double b) { return a / b; }
+    static __device__ __forceinline__ void len_inv_(double x, double& n, double& inv) {
+        n = sqrt(x);
+        inv = 1.0 / n;
+    }
+    static __device__ __forceinline__ double sqrt0_(double x) { return sqrt(x); }
+    static __device__ __forceinline__ void sincos_turn_(double u, double* s, double* c) {
+        sincos(2.0 * CUDART_PI * u, s, c);
+    }
 };
 
 template <typename T> struct V3 { T x, y, z; };
@@ -216,12 +237,14 @@ __device__ __forceinline__ V3<T> local_field(const Site& st, int half, const T* 
 template <typename T>
 __device__ __forceinline__ V3<T> hb_site(T beta, const V3<T>& S, uint32_t w0, uint32_t w1) {
     const T nS2 = dot(S, S);
-    const T nS = M<T>::sqrt_(nS2);
+    T nS;
     V3<T> n;
-    if (nS > (T)0) {
-        const T inv = (T)1 / nS;
+    if (nS2 > (T)0) {
+        T inv;
+        MX<T>::len_inv_(nS2, nS, inv);
         n.x = S.x * inv; n.y = S.y * inv; n.z = S.z * inv;
     } else {
+        nS = (T)0;
         n.x = (T)0; n.y = (T)0; n.z = (T)1;
     }
     const T R = beta * nS;
@@ -233,18 +256,17 @@ __device__ __forceinline__ V3<T> hb_site(T beta, const V3<T>& S, uint32_t w0, ui
         const T a = -M<T>::expm1_((T)-2 * R);
         const T qa = q * a;
         if (qa <= (T)0.5)
-            t = -M<T>::log1p_(-qa) / R;
+            t = MX<T>::div_(-M<T>::log1p_(-qa), R);
         else
-            t = -M<T>::log_(((T)1 - q) + q * M<T>::exp_((T)-2 * R)) / R;
+            t = MX<T>::div_(-M<T>::log_(((T)1 - q) + q * M<T>::exp_((T)-2 * R)), R);
     }
     t = t < (T)0 ? (T)0 : (t > (T)2 ? (T)2 : t);
     const T c = (T)1 - t;
-    const T st = M<T>::sqrt_(t * ((T)2 - t));
-    const T phi = (T)2 * M<T>::pi * ((T)(w1 >> 8) * (T)0x1p-24);
+    const T st = MX<T>::sqrt0_(t * ((T)2 - t));
     T sp, cp;
-    M<T>::sincos_(phi, &sp, &cp);
+    MX<T>::sincos_turn_((T)(w1 >> 8) * (T)0x1p-24, &sp, &cp);
     const T sgn = M<T>::copysign_((T)1, n.z);
-    const T a = (T)-1 / (sgn + n.z);
+    const T a = MX<T>::div_((T)-1, sgn + n.z);  // |sgn + n.z| >= 1
     const T b = n.x * n.y * a;
     const V3<T> e1 = {(T)1 + sgn * n.x * n.x * a, sgn * b, -sgn * n.x};
     const V3<T> e2 = {b, sgn + n.y * n.y * a, -n.y};
@@ -548,6 +570,21 @@ __device__ __forceinline__ VRow vrow(const SampleDesc& sd, int color, int h0) {
     return q;
 }
 
+// x 2^32 rounded to the nearest integer (ties to even) as a 64-bit integer,
+// for |x| < 2^31: the same value as the 64-bit conversion of x 2^32, built
+// from 32-bit conversions (GB300 runs 64-bit conversions on its narrow FP64
+// pipe).  The integer part t of x, the next 16 fraction bits u and the rest
+// are each exact in float (truncation only drops bits of x); only the last
+// piece is rounded, and the pieces above it are multiples of 2^16, so
+// rounding it rounds the whole.
+__device__ __forceinline__ long long fixed32(float x) {
+    const float t = truncf(x);
+    const float f = (x - t) * 65536.0f;
+    const float u = truncf(f);
+    const int c = __float2int_rn((f - u) * 65536.0f);
+    return (long long)(int)t * 4294967296LL + (long long)(int)u * 65536LL + (long long)c;
+}
+
 // ---------------------------------------------------------------------------
 // Deterministic block reduction of a double (blockDim.x multiple of 32,
 // <= 1024).  All threads must call it; the result is valid in thread 0.
@@ -619,8 +656,9 @@ __device__ __forceinline__ void acc_add(T& s, T& c, T x) {
 // by far) and added exactly: integer addition is associative, so the result
 // is the exact sum of the per-thread values for any reduction order or
 // cluster size, rounded once to double (exactly, while |total| < 2^21).  The
-// adds run on the integer pipe, not GB300's slow FP64 one.  Double values
-// take block_sum_multi.  Results valid in warp 0; sh holds NV * 32 doubles.
+// conversion (fixed32) and the adds run on the integer and FP32 pipes, not
+// GB300's narrow FP64 one.  Double values take block_sum_multi.  Results valid
+// in warp 0; sh holds NV * 32 doubles.
 template <typename T, int NV>
 __device__ __forceinline__ void block_sum_exact(const T (&v)[NV], double (&out)[NV], double* sh) {
     if (sizeof(T) == 8) {
@@ -633,7 +671,7 @@ __device__ __forceinline__ void block_sum_exact(const T (&v)[NV], double (&out)[
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-        long long x = __float2ll_rn((float)v[k] * 4294967296.0f);
+        long long x = fixed32((float)v[k]);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xFFFFFFFFu, x, o);
         if (lane == 0) shI[k * 32 + wid] = x;

@@ -28,7 +28,8 @@ constexpr int RES_THREADS = 512;
 
 // ENERGY (compile time, only the block's last half sweep) also returns the
 // thread's share of H in the spin precision: a few sites per thread, so at
-// most a few float terms meet before the block reduction carries on in double.
+// most a few float terms meet before the block adds the shares exactly
+// (block_sum_exact).
 template <typename T, int V, int KIND, bool ENERGY>
 __device__ __forceinline__ T res_halfsweep(T* __restrict__ sm, const float* __restrict__ J, const SampleDesc& sd,
                                            int color, T beta, unsigned long long seed, uint32_t sample,
@@ -240,7 +241,7 @@ __global__ void __launch_bounds__(RES_THREADS, 2) k_resident(DevBatch a, int n_h
         stv<T, VW>(g + q, v);
     }
     double H[1];
-    block_sum_multi<T, 1>(e, H, red);
+    block_sum_exact<T, 1>(e, H, red);
     if (threadIdx.x == 0) a.H[r] = H[0];
 }
 
@@ -547,7 +548,7 @@ __global__ void __launch_bounds__(NTH, 1024 / NTH) k_resident_cl(DevBatch a, int
         stv<T, VW>(gw + (long long)run * half + rank * hl + off, v);
     }
     double tot[1];
-    block_sum_multi<T, 1>(e, tot, red);
+    block_sum_exact<T, 1>(e, tot, red);
     if (threadIdx.x == 0) cta_total = tot[0];
     cl.sync();
     if (rank == 0 && threadIdx.x == 0) {

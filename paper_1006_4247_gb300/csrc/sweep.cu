@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(TILE, KIND == 1 ? 5 : 6) k_sweep(DevBatch a, c
     }
     if (ENERGY || KIND == 2) {
         double tot[1];
-        block_sum_multi<T, 1>(e, tot, sh);
+        block_sum_exact<T, 1>(e, tot, sh);
         if (threadIdx.x == 0) a.part[t] = tot[0];
     }
 }
