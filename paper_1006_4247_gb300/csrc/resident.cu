@@ -19,6 +19,7 @@
 
 #include "kernels.h"
 #include "pt_device.cuh"
+#include "tma.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -210,6 +211,7 @@ __global__ void __launch_bounds__(RES_THREADS, 2) k_resident(DevBatch a, int n_h
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw);
     __shared__ double red[32];
+    __shared__ __align__(8) unsigned long long io_bar;
     const int r = a.res_reps[a.rcl_begin[0] + (int)blockIdx.x];
     const int4 rd = a.reps[r];
     const SampleDesc& sd = a.samples[rd.x];
@@ -217,32 +219,44 @@ __global__ void __launch_bounds__(RES_THREADS, 2) k_resident(DevBatch a, int n_h
     const int n3 = 6 * half;  // elements of one replica
     const int nor = a.nor_s ? a.nor_s[rd.x] : n_or;
     T* g = (T*)a.spins + a.chain_off[rd.y] + (long long)a.bufmap[r] * (long long)n3;
-    constexpr int VW = 16 / sizeof(T);
-    for (int q = threadIdx.x * VW; q < n3; q += RES_THREADS * VW) {
-        T v[VW];
-        ldv<T, VW>(g + q, v);
-        stv<T, VW>(sm + q, v);
-    }
     // couplings after the spins (6 half floats; n3 * sizeof(T) is a multiple of 16 B)
     float* sJ = reinterpret_cast<float*>(sm + n3);
     const float* gJ = a.J + sd.J_off;
-    for (int q = threadIdx.x * 4; q < n3; q += RES_THREADS * 4) {
-        float v[4];
-        ldv_nc<float, 4>(gJ + q, v);
-        stv<float, 4>(sJ + q, v);
+    // The replica and its sample's couplings arrive by two bulk copies (one
+    // thread issues them; io_bar counts their bytes).  A block that starts
+    // with a heat-bath half sweep (colour 0) does not read colour 0's spins:
+    // that half sweep draws every one of them afresh.
+    const int skip = n_hb > 0 ? 3 * half : 0;
+    if (threadIdx.x == 0) {
+        mbar_init(&io_bar, 1);
+        fence_async_smem();
     }
     __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned sbytes = (unsigned)((n3 - skip) * (int)sizeof(T)), jbytes = (unsigned)n3 * 4u;
+        mbar_expect_tx(&io_bar, sbytes + jbytes);
+        bulk_g2s(sm + skip, g + skip, sbytes, &io_bar);
+        bulk_g2s(sJ, gJ, jbytes, &io_bar);
+    }
+    mbar_wait_io(&io_bar, 0u, a);
     T e[1];
     if (sizeof(T) == 4 && sd.vec == 4) e[0] = res_block<T, (sizeof(T) == 4 ? 4 : 2)>(sm, sJ, a, sd, rd, n_hb, nor);
     else e[0] = res_block<T, 2>(sm, sJ, a, sd, rd, n_hb, nor);
-    for (int q = threadIdx.x * VW; q < n3; q += RES_THREADS * VW) {
-        T v[VW];
-        ldv<T, VW>(sm + q, v);
-        stv<T, VW>(g + q, v);
+    // the final replica leaves by one bulk copy, after every thread's writes
+    // are made visible to the copy engine (res_block ends with a CTA barrier,
+    // the fence and the barrier below order the last half sweep's stores)
+    fence_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        bulk_s2g(g, sm, (unsigned)(n3 * (int)sizeof(T)));
+        bulk_commit();
     }
     double H[1];
     block_sum_exact<T, 1>(e, H, red);
-    if (threadIdx.x == 0) a.H[r] = H[0];
+    if (threadIdx.x == 0) {
+        a.H[r] = H[0];
+        bulk_wait_read();  // the shared memory stays until the copy has read it
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -502,6 +516,7 @@ __global__ void __launch_bounds__(NTH, 1024 / NTH) k_resident_cl(DevBatch a, int
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[32];
     __shared__ double cta_total;
+    __shared__ __align__(8) unsigned long long io_bar;
     cg::cluster_group cl = cg::this_cluster();
     const int cs = (int)cl.num_blocks(), rank = (int)cl.block_rank();
     const int r = a.res_reps[begin + (int)blockIdx.x / cs];
@@ -519,33 +534,41 @@ __global__ void __launch_bounds__(NTH, 1024 / NTH) k_resident_cl(DevBatch a, int
     float* sJ = reinterpret_cast<float*>(sm + n3);  // n3 * sizeof(T) is a multiple of 16 B
     const int nor = a.nor_s ? a.nor_s[rd.x] : n_or;
     // this CTA's slab: 6 contiguous runs of hl elements (colour, component)
-    const T* g = (const T*)a.spins + a.chain_off[rd.y] + (long long)a.bufmap[r] * (6LL * half);
+    // of the replica and of the couplings, fetched by bulk copies issued by
+    // one thread (io_bar counts their bytes); colour 0's spin runs are not
+    // read when the block starts with a heat-bath half sweep, which draws
+    // them afresh
+    T* g = (T*)a.spins + a.chain_off[rd.y] + (long long)a.bufmap[r] * (6LL * half);
     const float* gJ = a.J + sd.J_off;
-    constexpr int VW = 16 / sizeof(T);
-    for (int q = threadIdx.x * VW; q < n3; q += NTH * VW) {
-        const int run = q / hl, off = q - run * hl;  // hl is a multiple of VW
-        T v[VW];
-        ldv<T, VW>(g + (long long)run * half + rank * hl + off, v);
-        stv<T, VW>(sm + q, v);
+    if (threadIdx.x == 0) {
+        mbar_init(&io_bar, 1);
+        fence_async_smem();
     }
-    for (int q = threadIdx.x * 4; q < n3; q += NTH * 4) {
-        const int run = q / hl, off = q - run * hl;
-        float v[4];
-        ldv_nc<float, 4>(gJ + (long long)run * half + rank * hl + off, v);
-        stv<float, 4>(sJ + q, v);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int run0 = n_hb > 0 ? 3 : 0;
+        const unsigned sb = (unsigned)(hl * (int)sizeof(T)), jb = (unsigned)hl * 4u;
+        mbar_expect_tx(&io_bar, (unsigned)(6 - run0) * sb + 6u * jb);
+        for (int run = run0; run < 6; ++run)
+            bulk_g2s(sm + run * hl, g + (long long)run * half + rank * hl, sb, &io_bar);
+        for (int run = 0; run < 6; ++run)
+            bulk_g2s(sJ + run * hl, gJ + (long long)run * half + rank * hl, jb, &io_bar);
     }
+    mbar_wait_io(&io_bar, 0u, a);
     cl.sync();  // every slab loaded before any neighbour reads it
     T e[1];
     if (sizeof(T) == 4 && sd.vec == 4)
         e[0] = cl_block<T, NTH, (sizeof(T) == 4 ? 4 : 2)>(cl, sm, sJ, a, sd, sb, rd, n_hb, nor);
     else e[0] = cl_block<T, NTH, 2>(cl, sm, sJ, a, sd, sb, rd, n_hb, nor);
-    // the last barrier of the block has passed: the slab is final
-    T* gw = (T*)a.spins + a.chain_off[rd.y] + (long long)a.bufmap[r] * (6LL * half);
-    for (int q = threadIdx.x * VW; q < n3; q += NTH * VW) {
-        const int run = q / hl, off = q - run * hl;
-        T v[VW];
-        ldv<T, VW>(sm + q, v);
-        stv<T, VW>(gw + (long long)run * half + rank * hl + off, v);
+    // the last barrier of the block has passed: the slab is final; it leaves
+    // by bulk copies after the fence makes every thread's writes visible to
+    // the copy engine
+    fence_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int run = 0; run < 6; ++run)
+            bulk_s2g(g + (long long)run * half + rank * hl, sm + run * hl, (unsigned)(hl * (int)sizeof(T)));
+        bulk_commit();
     }
     double tot[1];
     block_sum_exact<T, 1>(e, tot, red);
@@ -556,6 +579,7 @@ __global__ void __launch_bounds__(NTH, 1024 / NTH) k_resident_cl(DevBatch a, int
         for (int q = 0; q < cs; ++q) H += *cl.map_shared_rank(&cta_total, q);
         a.H[r] = H;
     }
+    if (threadIdx.x == 0) bulk_wait_read();  // the slab stays until its copies have read it
     cl.sync();  // no CTA leaves while rank 0 reads its total
 }
 
