@@ -15,6 +15,7 @@
 #include "kernels.h"
 #include "exchange_common.cuh"
 #include "pt_device.cuh"
+#include "tma.cuh"
 
 namespace ptk {
 
@@ -95,8 +96,8 @@ constexpr int HP_THREADS = 256;
 // in shared memory, over V-site vectors: the sites of colour `col` of `src`
 // are transformed into `dst` (dst may equal src), the field coming from the
 // other colour of `field`.  Adds ln det J_f to lj and, with ENERGY, -s.S of
-// the new spins to e.
-template <typename T, int V, bool COOL, bool ENERGY>
+// the new spins to e.  JS: the couplings J0, J1 are in shared memory too.
+template <typename T, int V, bool COOL, bool ENERGY, bool JS = false>
 __device__ __forceinline__ void ch_colour(const SampleDesc& sd, const T* field, const T* src, T* dst,
                                           const float* J0, const float* J1, int col, T eps, T& lj, T& e) {
     const int half = sd.half;
@@ -106,7 +107,7 @@ __device__ __forceinline__ void ch_colour(const SampleDesc& sd, const T* field, 
     for (int h0 = (int)threadIdx.x * V; h0 < half; h0 += (int)blockDim.x * V) {
         const VRow q = vrow<V>(sd, col, h0);
         T S[3][V], s[3][V];
-        nbr_field<T, V>(fo, Jown, Joth, half, h0, q.xs, q.hyp, q.hym, q.hzp, q.hzm, q.p, S);
+        nbr_field<T, V, JS>(fo, Jown, Joth, half, h0, q.xs, q.hyp, q.hym, q.hzp, q.hzm, q.p, S);
 #pragma unroll
         for (int c = 0; c < 3; ++c) ldv<T, V>(src + col * 3 * half + c * half + h0, s[c]);
 #pragma unroll
@@ -155,6 +156,76 @@ __global__ void __launch_bounds__(HP_THREADS) k_heat_pre(DevBatch a) {
         a.heat_lnJ[pair] = tot[0];
         a.heat_H[pair] = tot[1];
     }
+}
+
+// The same heated proposal with the configuration and its sample's couplings
+// staged in shared memory (two bulk copies, io_bar counts their bytes) where
+// both fit one SM: colour 1 then colour 0 are transformed in place (each site
+// reads its own spin and neighbours of the other colour, which that pass does
+// not change), and the result leaves by one bulk copy.  The neighbour gathers
+// then wait on shared memory instead of L2.
+constexpr int HS_THREADS = 512;
+
+template <typename T, int V>
+__device__ __forceinline__ void heat_pass_smem(const SampleDesc& sd, T* cfg, const float* sJ, T eps, T (&part)[2]) {
+    const int half = sd.half;
+    T none = (T)0;
+    ch_colour<T, V, false, false, true>(sd, cfg, cfg, cfg, sJ, sJ + 3 * half, 1, eps, part[0], none);
+    __syncthreads();
+    ch_colour<T, V, false, true, true>(sd, cfg, cfg, cfg, sJ, sJ + 3 * half, 0, eps, part[0], part[1]);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(HS_THREADS, sizeof(T) == 4 ? 2 : 1) k_heat_pre_smem(DevBatch a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[2 * 32];
+    __shared__ __align__(8) unsigned long long io_bar;
+    const int ch = blockIdx.x, i = blockIdx.y;
+    const ChainDesc cd = a.chains[ch];
+    const SampleDesc& sd = a.samples[cd.s];
+    if (i + 1 >= sd.NT) return;  // uniform over the block
+    const int half = sd.half, n3 = 6 * half;
+    const T* src = (const T*)a.spins + a.chain_off[ch] + (long long)a.bufmap[cd.r0 + i + 1] * n3;
+    const long long pair = cd.pair_off + i;
+    T* out = (T*)a.heat_buf + pair * (6LL * a.max_half);
+    T* cfg = reinterpret_cast<T*>(smem_raw);
+    float* sJ = reinterpret_cast<float*>(cfg + n3);  // n3 * sizeof(T) is a multiple of 16 B
+    if (threadIdx.x == 0) {
+        mbar_init(&io_bar, 1);
+        fence_async_smem();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned sb = (unsigned)(n3 * (int)sizeof(T)), jb = (unsigned)n3 * 4u;
+        mbar_expect_tx(&io_bar, sb + jb);
+        bulk_g2s(cfg, src, sb, &io_bar);
+        bulk_g2s(sJ, a.J + sd.J_off, jb, &io_bar);
+    }
+    const T eps = (T)a.eps[sd.eps_off + i];
+    mbar_wait_io(&io_bar, 0u, a);
+    T part[2] = {(T)0, (T)0};  // ln det J_C, energy
+    if (sizeof(T) == 4 && sd.vec == 4) heat_pass_smem<T, (sizeof(T) == 4 ? 4 : 2)>(sd, cfg, sJ, eps, part);
+    else if (sd.hL % 2 == 0) heat_pass_smem<T, 2>(sd, cfg, sJ, eps, part);
+    else heat_pass_smem<T, 1>(sd, cfg, sJ, eps, part);
+    fence_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        bulk_s2g(out, cfg, (unsigned)(n3 * (int)sizeof(T)));
+        bulk_commit();
+    }
+    double tot[2];
+    block_sum_exact<T, 2>(part, tot, red);
+    if (threadIdx.x == 0) {
+        a.heat_lnJ[pair] = tot[0];
+        a.heat_H[pair] = tot[1];
+        bulk_wait_read();
+    }
+}
+
+// Configuration and couplings of the largest sample within one CTA's shared
+// memory (with room for the static tables).
+static bool heat_pre_staged(int max_half, bool fp64) {
+    return (size_t)6 * max_half * ((fp64 ? 8 : 4) + 4) <= 200 * 1024;
 }
 
 // Asynchronous 16-byte global -> shared copies (cp.async, cache-global) of n
@@ -411,14 +482,28 @@ cudaError_t launch_exchange_smem(const DevBatch& b, bool fp64, int mode, int max
         const dim3 grid_pre((unsigned)b.n_chains, (unsigned)(b.max_NT - 1), 1);
         const int three = coolheat_three_slots(max_half, fp64) ? 1 : 0;
         const size_t smem_w = three ? smem / 2 * 3 : smem;
+        const bool staged = heat_pre_staged(max_half, fp64);
+        const size_t smem_pre = (size_t)6 * max_half * ((fp64 ? 8 : 4) + 4);
         if (fp64) {
-            k_heat_pre<double><<<grid_pre, HP_THREADS, 0, st>>>(b);
+            if (staged) {
+                e = ensure_smem((const void*)k_heat_pre_smem<double>, smem_pre);
+                if (e != cudaSuccess) return e;
+                k_heat_pre_smem<double><<<grid_pre, HS_THREADS, smem_pre, st>>>(b);
+            } else {
+                k_heat_pre<double><<<grid_pre, HP_THREADS, 0, st>>>(b);
+            }
             e = ensure_smem((const void*)k_exchange_coolheat_smem<double>, smem_w);
             if (e != cudaSuccess) return e;
             k_exchange_coolheat_smem<double><<<b.n_chains, SX_THREADS, smem_w, st>>>(b, three);
             k_heat_commit<double><<<grid_pre, HP_THREADS, 0, st>>>(b);
         } else {
-            k_heat_pre<float><<<grid_pre, HP_THREADS, 0, st>>>(b);
+            if (staged) {
+                e = ensure_smem((const void*)k_heat_pre_smem<float>, smem_pre);
+                if (e != cudaSuccess) return e;
+                k_heat_pre_smem<float><<<grid_pre, HS_THREADS, smem_pre, st>>>(b);
+            } else {
+                k_heat_pre<float><<<grid_pre, HP_THREADS, 0, st>>>(b);
+            }
             e = ensure_smem((const void*)k_exchange_coolheat_smem<float>, smem_w);
             if (e != cudaSuccess) return e;
             k_exchange_coolheat_smem<float><<<b.n_chains, SX_THREADS, smem_w, st>>>(b, three);
