@@ -156,8 +156,9 @@ __device__ __forceinline__ T res_or_one(T* __restrict__ sm, const float* __restr
 }
 
 // The sweep block of one replica (the CTA's replica is held in `sm`).  Heat-
-// bath half sweeps (1 of 1 + 5L/4 sweeps) run one site per thread so that the
-// register peak is set by the vectorised overrelaxation path.
+// bath half sweeps run on the same V-site vectors as the overrelaxation ones
+// (vector loads, row indices once per vector; the draws and arithmetic per
+// site are unchanged).
 template <typename T, int V>
 __device__ __forceinline__ T res_block(T* sm, const float* J, const DevBatch& a, const SampleDesc& sd,
                                        const int4& rd, int n_hb, int n_or) {
@@ -170,9 +171,9 @@ __device__ __forceinline__ T res_block(T* sm, const float* J, const DevBatch& a,
         for (int c = 0; c < 2; ++c, ++kstep) {
             const unsigned long long st = step0 + (unsigned long long)kstep;
             if (kstep == total - 1)
-                e = res_halfsweep<T, 1, 1, true>(sm, J, sd, c, beta, a.seed, (uint32_t)rd.x, (uint32_t)rd.w, st);
+                e = res_halfsweep<T, V, 1, true>(sm, J, sd, c, beta, a.seed, (uint32_t)rd.x, (uint32_t)rd.w, st);
             else
-                res_halfsweep<T, 1, 1, false>(sm, J, sd, c, beta, a.seed, (uint32_t)rd.x, (uint32_t)rd.w, st);
+                res_halfsweep<T, V, 1, false>(sm, J, sd, c, beta, a.seed, (uint32_t)rd.x, (uint32_t)rd.w, st);
             __syncthreads();
         }
     if (sd.half <= RES_THREADS * V) {
@@ -460,6 +461,9 @@ __device__ __forceinline__ T cl_or_one(cg::cluster_group& cl, T* __restrict__ sm
     return e;
 }
 
+// The heat-bath half sweeps of the cluster block run one site per thread: on
+// the overrelaxation path's vectors they are cheaper themselves but raise the
+// kernel's register demand, and the overrelaxation sweeps then spill.
 template <typename T, int NTH, int V>
 __device__ __forceinline__ T cl_block(cg::cluster_group& cl, T* sm, const float* J, const DevBatch& a,
                                       const SampleDesc& sd, const Slab& sb, const int4& rd, int n_hb, int n_or) {
