@@ -73,7 +73,7 @@ def load_peaks():
 
 KERNEL_SOURCES = {
     "k_sweep": ("sweep.cu", "pt_device.cuh", "pt_types.h", "kernels.h"),
-    "k_resident": ("resident.cu", "pt_device.cuh", "pt_types.h", "kernels.h"),
+    "k_resident": ("resident.cu", "pt_device.cuh", "tma.cuh", "pt_types.h", "kernels.h"),
 }
 
 
