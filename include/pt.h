@@ -248,19 +248,24 @@ typedef enum { PT_POLICY_AUTO = 0, PT_POLICY_STREAMING = 1, PT_POLICY_RESIDENT =
 pt_status pt_set_policy(pt_handle h, int policy);
 
 /* Bounded device-side waits and a hook to test their failure path.
- * The only kernel that waits on the device is the bulk-copy (TMA) half sweep
- * of overrelaxation (selected by PT_TMA=1 in the environment when the handle
- * is created; FP32, every L a multiple of 8, streaming policy): each of its
- * mbarrier waits polls at most `limit` times (0 restores the default, 2^22),
- * then sets the handle's device error word, lets the copies it has in flight
- * land and returns; the next call that synchronises (pt_measure, pt_get_spins,
- * pt_get_stats, ...) returns PT_ERR_TIMEOUT once and clears the word.  The
- * spins of the half sweep that gave up are left partly updated (each still a
- * valid unit vector); the handle stays usable.
- * inject != 0 makes every later launch of that kernel leave the copies of one
- * stage un-issued (first replica of the first work item of CTA 0), so the wait
- * for it runs out; inject = 0 turns that off.  PT_ERR_STATE if inject != 0 and
- * the handle does not use the bulk-copy half sweep. */
+ * The kernels that wait on the device are those that move data with TMA bulk
+ * copies and wait for them on an mbarrier: the resident sweep blocks (one CTA
+ * or a cluster per replica; their replica's load), the staged heated-proposal
+ * pass of the cooling/heating exchange, and the bulk-copy (TMA) half sweep of
+ * overrelaxation (selected by PT_TMA=1 in the environment when the handle is
+ * created; FP32, every L a multiple of 8, streaming policy).  Each wait polls
+ * at most `limit` times (0 restores the default, 2^22), then sets the handle's
+ * device error word, gives the copies in flight a bounded chance to land and
+ * skips the work that needed them: a resident block leaves its replica in
+ * global memory as it was (a cluster does so as a whole), the half sweep
+ * leaves the replicas it did not reach; every spin stays a valid unit vector.
+ * The next call that synchronises (pt_measure, pt_get_spins, pt_get_stats,
+ * ...) returns PT_ERR_TIMEOUT once and clears the word; the handle stays
+ * usable.  inject != 0 makes CTA 0 of every later launch of those kernels
+ * leave its copies un-issued (for the half sweep: one stage of the first
+ * replica of its first work item), so its wait runs out; inject = 0 turns that
+ * off.  PT_ERR_STATE if inject != 0 and the handle currently runs none of
+ * them (no resident sample and no bulk-copy half sweep). */
 pt_status pt_set_wait_limit(pt_handle h, unsigned long long limit, int inject);
 
 /* Energies H = -sum_<xy> J_xy s_x . s_y of configurations that live in the

@@ -1315,8 +1315,8 @@ pt_status pt_set_policy(pt_handle e, int policy) {
 
 pt_status pt_set_wait_limit(pt_handle e, unsigned long long limit, int inject) {
     if (!e) return fail(PT_ERR_ARG, "NULL handle");
-    if (inject && (!e->all_tma || e->tma_items.empty()))
-        return fail(PT_ERR_STATE, "the batch does not use the bulk-copy half sweep");
+    if (inject && (!e->all_tma || e->tma_items.empty()) && e->res_reps.empty())
+        return fail(PT_ERR_STATE, "the batch runs no bulk-copy kernel (neither resident sweeps nor the bulk-copy half sweep)");
     pt_status st = sync(e);
     if (st != PT_OK) return st;
     e->d.wait_limit = limit ? limit : WAIT_LIMIT_DEFAULT;

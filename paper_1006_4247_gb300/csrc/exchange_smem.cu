@@ -198,11 +198,22 @@ __global__ void __launch_bounds__(HS_THREADS, sizeof(T) == 4 ? 2 : 1) k_heat_pre
     if (threadIdx.x == 0) {
         const unsigned sb = (unsigned)(n3 * (int)sizeof(T)), jb = (unsigned)n3 * 4u;
         mbar_expect_tx(&io_bar, sb + jb);
-        bulk_g2s(cfg, src, sb, &io_bar);
-        bulk_g2s(sJ, a.J + sd.J_off, jb, &io_bar);
+        // failure-path test hook: block (0, 0) leaves its copies un-issued, so its wait runs out
+        if (!(a.wait_fault && blockIdx.x == 0 && blockIdx.y == 0)) {
+            bulk_g2s(cfg, src, sb, &io_bar);
+            bulk_g2s(sJ, a.J + sd.J_off, jb, &io_bar);
+        }
     }
     const T eps = (T)a.eps[sd.eps_off + i];
-    mbar_wait_io(&io_bar, 0u, a);
+    if (__syncthreads_or(!mbar_wait_io(&io_bar, 0u, a, !(a.wait_fault && blockIdx.x == 0 && blockIdx.y == 0)))) {
+        // gave up (error word set): no proposal; an infinite energy makes the
+        // walk reject the pair (ln A = -inf, or NaN at beta = 0: never accepted)
+        if (threadIdx.x == 0) {
+            a.heat_H[pair] = __longlong_as_double(0x7FF0000000000000LL);
+            a.heat_lnJ[pair] = 0.0;
+        }
+        return;
+    }
     T part[2] = {(T)0, (T)0};  // ln det J_C, energy
     if (sizeof(T) == 4 && sd.vec == 4) heat_pass_smem<T, (sizeof(T) == 4 ? 4 : 2)>(sd, cfg, sJ, eps, part);
     else if (sd.hL % 2 == 0) heat_pass_smem<T, 2>(sd, cfg, sJ, eps, part);

@@ -56,7 +56,7 @@ struct DevBatch {
     int max_half;                   // largest L^3/2 of the batch
     int* err;                       // device error word (bit 0: a bounded wait gave up)
     unsigned long long wait_limit;  // polls of a bounded mbarrier wait before it gives up
-    int wait_fault;                 // test hook: the bulk-copy half sweep leaves one stage un-issued
+    int wait_fault;                 // test hook: CTA 0 of a bulk-copy kernel leaves its copies un-issued
     const int4* tma_items;          // (sample, k0, first replica, count) of the bulk-copy half sweep
     int n_tma_items;
     int tma_smem;                   // dynamic shared memory of the bulk-copy half sweep

@@ -236,10 +236,14 @@ __global__ void __launch_bounds__(RES_THREADS, 2) k_resident(DevBatch a, int n_h
     if (threadIdx.x == 0) {
         const unsigned sbytes = (unsigned)((n3 - skip) * (int)sizeof(T)), jbytes = (unsigned)n3 * 4u;
         mbar_expect_tx(&io_bar, sbytes + jbytes);
-        bulk_g2s(sm + skip, g + skip, sbytes, &io_bar);
-        bulk_g2s(sJ, gJ, jbytes, &io_bar);
+        // failure-path test hook: CTA 0 leaves its copies un-issued, so its wait runs out
+        if (!(a.wait_fault && blockIdx.x == 0)) {
+            bulk_g2s(sm + skip, g + skip, sbytes, &io_bar);
+            bulk_g2s(sJ, gJ, jbytes, &io_bar);
+        }
     }
-    mbar_wait_io(&io_bar, 0u, a);
+    // a wait that gave up leaves the replica in global memory as it was
+    if (__syncthreads_or(!mbar_wait_io(&io_bar, 0u, a, !(a.wait_fault && blockIdx.x == 0)))) return;
     T e[1];
     if (sizeof(T) == 4 && sd.vec == 4) e[0] = res_block<T, (sizeof(T) == 4 ? 4 : 2)>(sm, sJ, a, sd, rd, n_hb, nor);
     else e[0] = res_block<T, 2>(sm, sJ, a, sd, rd, n_hb, nor);
@@ -520,6 +524,7 @@ __global__ void __launch_bounds__(NTH, 1024 / NTH) k_resident_cl(DevBatch a, int
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[32];
     __shared__ double cta_total;
+    __shared__ int cta_failed;
     __shared__ __align__(8) unsigned long long io_bar;
     cg::cluster_group cl = cg::this_cluster();
     const int cs = (int)cl.num_blocks(), rank = (int)cl.block_rank();
@@ -553,13 +558,27 @@ __global__ void __launch_bounds__(NTH, 1024 / NTH) k_resident_cl(DevBatch a, int
         const int run0 = n_hb > 0 ? 3 : 0;
         const unsigned sb = (unsigned)(hl * (int)sizeof(T)), jb = (unsigned)hl * 4u;
         mbar_expect_tx(&io_bar, (unsigned)(6 - run0) * sb + 6u * jb);
-        for (int run = run0; run < 6; ++run)
-            bulk_g2s(sm + run * hl, g + (long long)run * half + rank * hl, sb, &io_bar);
-        for (int run = 0; run < 6; ++run)
-            bulk_g2s(sJ + run * hl, gJ + (long long)run * half + rank * hl, jb, &io_bar);
+        // failure-path test hook: the first CTA of the launch leaves its copies
+        // un-issued, so its wait runs out
+        if (!(a.wait_fault && blockIdx.x == 0)) {
+            for (int run = run0; run < 6; ++run)
+                bulk_g2s(sm + run * hl, g + (long long)run * half + rank * hl, sb, &io_bar);
+            for (int run = 0; run < 6; ++run)
+                bulk_g2s(sJ + run * hl, gJ + (long long)run * half + rank * hl, jb, &io_bar);
+        }
     }
-    mbar_wait_io(&io_bar, 0u, a);
-    cl.sync();  // every slab loaded before any neighbour reads it
+    const int failed = __syncthreads_or(!mbar_wait_io(&io_bar, 0u, a, !(a.wait_fault && blockIdx.x == 0)));
+    if (threadIdx.x == 0) cta_failed = failed;
+    cl.sync();  // every slab loaded (or given up) before any neighbour reads it
+    // a wait that gave up anywhere in the cluster: every CTA of it sees the
+    // same flags and skips the block, leaving the replica in global memory as
+    // it was (one more barrier: no CTA leaves while another reads its flag)
+    int any_failed = 0;
+    for (int q = 0; q < cs; ++q) any_failed |= *cl.map_shared_rank(&cta_failed, q);
+    if (any_failed) {
+        cl.sync();
+        return;
+    }
     T e[1];
     if (sizeof(T) == 4 && sd.vec == 4)
         e[0] = cl_block<T, NTH, (sizeof(T) == 4 ? 4 : 2)>(cl, sm, sJ, a, sd, sb, rd, n_hb, nor);

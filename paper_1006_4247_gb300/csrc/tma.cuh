@@ -62,13 +62,17 @@ __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.comm
 __device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 
 // Bounded wait by every calling thread for phase `parity` of an mbarrier that
-// counts the bytes of bulk loads.  If the wait gives up, the error word gets
-// bit 0 and a second bounded wait gives the copies in flight a chance to land
-// before the caller goes on (and, eventually, releases the shared memory).
-__device__ __forceinline__ void mbar_wait_io(unsigned long long* bar, unsigned parity, const DevBatch& a) {
-    if (mbar_wait_bounded(bar, parity, a.wait_limit)) return;
+// counts the bytes of bulk loads; true if the phase completed.  If the wait
+// gives up, the error word gets bit 0 and, when copies were issued, a second
+// bounded wait gives them a chance to land before the caller skips the work
+// that needed them (and, eventually, releases the shared memory).  Threads
+// may disagree, so callers combine the results over the CTA (or cluster).
+__device__ __forceinline__ bool mbar_wait_io(unsigned long long* bar, unsigned parity, const DevBatch& a,
+                                             bool issued = true) {
+    if (mbar_wait_bounded(bar, parity, a.wait_limit)) return true;
     atomicOr(a.err, 1);
-    mbar_wait_bounded(bar, parity, a.wait_limit > WAIT_LIMIT_DEFAULT ? a.wait_limit : WAIT_LIMIT_DEFAULT);
+    if (issued) mbar_wait_bounded(bar, parity, a.wait_limit > WAIT_LIMIT_DEFAULT ? a.wait_limit : WAIT_LIMIT_DEFAULT);
+    return false;
 }
 
 }  // namespace ptk

@@ -215,10 +215,46 @@ def test_bounded_wait_gives_up_and_handle_stays_usable(monkeypatch):
     eng.close()
     ref.close()
     plain, _, _ = make_engine(8, 1, 3, 2, "fp32")
+    plain.set_policy("streaming")
     with pytest.raises(pt.PtError) as ei:
-        plain.set_wait_limit(16, inject=True)  # no bulk-copy kernel to fault
+        plain.set_wait_limit(16, inject=True)  # streaming without bulk copies: nothing to fault
     assert ei.value.status == pt.PT_ERR_STATE
     plain.close()
+
+
+@pytest.mark.parametrize("L", [16, 32])
+def test_resident_wait_gives_up_and_leaves_replica(L):
+    """The resident block's bulk-copy wait runs out for CTA 0 (L = 16: one CTA
+    per replica) or for the first cluster (L = 32): the next synchronising call
+    returns PT_ERR_TIMEOUT once, the replica whose copies never came is left as
+    it was (the whole cluster skips its block), every spin stays a unit
+    vector, and the handle then sweeps exactly like one that never failed."""
+    from gpu_util import set_random_state
+    S, NT, C = 1, 2, 2
+    eng, J, B = make_engine(L, S, NT, C, "fp32", seed=5)
+    eng.set_policy("resident")
+    ref, _, _ = make_engine(L, S, NT, C, "fp32", seed=5)
+    ref.set_policy("resident")
+    before = get_state(eng, S, C, NT)
+    eng.set_wait_limit(1024, inject=True)
+    eng.sweep(1, 2)
+    ref.sweep(1, 2)  # the same step count on both handles
+    with pytest.raises(pt.PtError) as ei:
+        eng.energies()
+    assert ei.value.status == pt.PT_ERR_TIMEOUT
+    after = get_state(eng, S, C, NT)
+    assert np.array_equal(after[0, 0, 0], before[0, 0, 0])  # the first replica: CTA 0's
+    assert np.abs(np.linalg.norm(after, axis=-1) - 1.0).max() < 1e-5
+    eng.set_wait_limit(0, inject=False)
+    out = []
+    for e in (eng, ref):
+        set_random_state(e, S, C, NT, L, seed=23)
+        e.sweep(1, 2)
+        out.append((get_state(e, S, C, NT), e.energies()))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
+    eng.close()
+    ref.close()
 
 
 def test_set_paths_and_cached_autotune(tmp_path):
