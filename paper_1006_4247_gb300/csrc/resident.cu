@@ -4,8 +4,8 @@
 //
 // For small lattices a replica fits on chip (L = 16: 4096 sites x 12 B =
 // 48 KB in float), so instead of 2 (n_hb + n_or) passes over HBM the block is
-// read once, all half sweeps run out of shared memory with a CTA barrier
-// between colours, and the result is written once.  The energy of the final
+// read once (TMA bulk copies), all half sweeps run out of shared memory with a
+// CTA barrier between colours, and the result is written once (one bulk copy).  The energy of the final
 // configuration is reduced during the last half sweep (every bond has exactly
 // one colour-1 end) and written straight to H[r].
 //
