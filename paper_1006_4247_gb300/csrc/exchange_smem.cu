@@ -85,7 +85,7 @@ __device__ __forceinline__ T sx_decim_D(T n, T b1, T b2, T db, T lr) {
 // ---------------------------------------------------------------------------
 // Cooling/heating (section III.B).  The heated proposal of pair i is
 // C^-1 of the configuration at beta_{i+1}, which no earlier pair of the update
-// touches: k_heat_pre computes it for every pair of every chain at once (with
+// touches: k_heat_pre_smem computes it for every pair of every chain at once (with
 // its energy and ln det J_C), and k_exchange_coolheat_smem then walks the
 // pairs of each chain in order, cooling the configuration at beta_i (which
 // does depend on the earlier decisions) in shared memory.
@@ -125,45 +125,12 @@ __device__ __forceinline__ void ch_colour(const SampleDesc& sd, const T* field, 
 
 // Heated proposal of pair i (blockIdx.y) of chain blockIdx.x: C^-1 = colour
 // 1 then colour 0 of the inverse step on the configuration at beta_{i+1},
-// with eps_i, read from the pool and written straight to the proposal buffer
-// (the second colour's field is the first colour's output, visible to the
-// block after the barrier).
-template <typename T>
-__global__ void __launch_bounds__(HP_THREADS) k_heat_pre(DevBatch a) {
-    __shared__ double red[2 * 32];
-    const int ch = blockIdx.x, i = blockIdx.y;
-    const ChainDesc cd = a.chains[ch];
-    const SampleDesc& sd = a.samples[cd.s];
-    if (i + 1 >= sd.NT) return;  // uniform over the block
-    const int half = sd.half, n3 = 6 * half;
-    const T* src = (const T*)a.spins + a.chain_off[ch] + (long long)a.bufmap[cd.r0 + i + 1] * n3;
-    const long long pair = cd.pair_off + i;
-    T* out = (T*)a.heat_buf + pair * (6LL * a.max_half);
-    const float* J0 = a.J + sd.J_off;
-    const float* J1 = a.J + sd.J_off + 3 * half;
-    const T eps = (T)a.eps[sd.eps_off + i];
-    T part[2] = {(T)0, (T)0};  // ln det J_C, energy
-    T none = (T)0;
-    const bool v2 = (sd.hL % 2) == 0;
-    if (v2) ch_colour<T, 2, false, false>(sd, src, src, out, J0, J1, 1, eps, part[0], none);
-    else ch_colour<T, 1, false, false>(sd, src, src, out, J0, J1, 1, eps, part[0], none);
-    __syncthreads();
-    if (v2) ch_colour<T, 2, false, true>(sd, out, src, out, J0, J1, 0, eps, part[0], part[1]);
-    else ch_colour<T, 1, false, true>(sd, out, src, out, J0, J1, 0, eps, part[0], part[1]);
-    double tot[2];
-    block_sum_exact<T, 2>(part, tot, red);
-    if (threadIdx.x == 0) {
-        a.heat_lnJ[pair] = tot[0];
-        a.heat_H[pair] = tot[1];
-    }
-}
-
-// The same heated proposal with the configuration and its sample's couplings
-// staged in shared memory (two bulk copies, io_bar counts their bytes) where
-// both fit one SM: colour 1 then colour 0 are transformed in place (each site
-// reads its own spin and neighbours of the other colour, which that pass does
-// not change), and the result leaves by one bulk copy.  The neighbour gathers
-// then wait on shared memory instead of L2.
+// with eps_i.  The configuration and its sample's couplings are staged in
+// shared memory (two bulk copies, io_bar counts their bytes; they fit one SM
+// wherever the staged walk does): colour 1 then colour 0 are transformed in
+// place (each site reads its own spin and neighbours of the other colour,
+// which that pass does not change), and the result leaves by one bulk copy
+// into the proposal buffer.
 constexpr int HS_THREADS = 512;
 
 template <typename T, int V>
@@ -231,12 +198,6 @@ __global__ void __launch_bounds__(HS_THREADS, sizeof(T) == 4 ? 2 : 1) k_heat_pre
         a.heat_H[pair] = tot[1];
         bulk_wait_read();
     }
-}
-
-// Configuration and couplings of the largest sample within one CTA's shared
-// memory (with room for the static tables).
-static bool heat_pre_staged(int max_half, bool fp64) {
-    return (size_t)6 * max_half * ((fp64 ? 8 : 4) + 4) <= 200 * 1024;
 }
 
 // Asynchronous 16-byte global -> shared copies (cp.async, cache-global) of n
@@ -493,28 +454,21 @@ cudaError_t launch_exchange_smem(const DevBatch& b, bool fp64, int mode, int max
         const dim3 grid_pre((unsigned)b.n_chains, (unsigned)(b.max_NT - 1), 1);
         const int three = coolheat_three_slots(max_half, fp64) ? 1 : 0;
         const size_t smem_w = three ? smem / 2 * 3 : smem;
-        const bool staged = heat_pre_staged(max_half, fp64);
+        // configuration and couplings of the largest sample: 6 half (size of T + 4) bytes,
+        // within one CTA wherever two configurations fit the walk's slots
         const size_t smem_pre = (size_t)6 * max_half * ((fp64 ? 8 : 4) + 4);
         if (fp64) {
-            if (staged) {
-                e = ensure_smem((const void*)k_heat_pre_smem<double>, smem_pre);
-                if (e != cudaSuccess) return e;
-                k_heat_pre_smem<double><<<grid_pre, HS_THREADS, smem_pre, st>>>(b);
-            } else {
-                k_heat_pre<double><<<grid_pre, HP_THREADS, 0, st>>>(b);
-            }
+            e = ensure_smem((const void*)k_heat_pre_smem<double>, smem_pre);
+            if (e != cudaSuccess) return e;
+            k_heat_pre_smem<double><<<grid_pre, HS_THREADS, smem_pre, st>>>(b);
             e = ensure_smem((const void*)k_exchange_coolheat_smem<double>, smem_w);
             if (e != cudaSuccess) return e;
             k_exchange_coolheat_smem<double><<<b.n_chains, SX_THREADS, smem_w, st>>>(b, three);
             k_heat_commit<double><<<grid_pre, HP_THREADS, 0, st>>>(b);
         } else {
-            if (staged) {
-                e = ensure_smem((const void*)k_heat_pre_smem<float>, smem_pre);
-                if (e != cudaSuccess) return e;
-                k_heat_pre_smem<float><<<grid_pre, HS_THREADS, smem_pre, st>>>(b);
-            } else {
-                k_heat_pre<float><<<grid_pre, HP_THREADS, 0, st>>>(b);
-            }
+            e = ensure_smem((const void*)k_heat_pre_smem<float>, smem_pre);
+            if (e != cudaSuccess) return e;
+            k_heat_pre_smem<float><<<grid_pre, HS_THREADS, smem_pre, st>>>(b);
             e = ensure_smem((const void*)k_exchange_coolheat_smem<float>, smem_w);
             if (e != cudaSuccess) return e;
             k_exchange_coolheat_smem<float><<<b.n_chains, SX_THREADS, smem_w, st>>>(b, three);
