@@ -328,11 +328,14 @@ def test_uneven_batch_parity():
     eng.close()
 
 
-@pytest.mark.parametrize("L", [8, 16, 24, 32])
-def test_resident_and_streaming_paths_fp64(L):
-    """A block of 1 heat-bath + 3 overrelaxation sweeps through the
+@pytest.mark.parametrize("L,n_hb,n_or", [(8, 1, 3), (16, 1, 3), (24, 1, 3), (32, 1, 3),
+                                         (16, 2, 1), (16, 0, 2), (32, 2, 1), (32, 0, 2)])
+def test_resident_and_streaming_paths_fp64(L, n_hb, n_or):
+    """A block of n_hb heat-bath + n_or overrelaxation sweeps through the
     shared-memory resident kernel and through the streaming half sweeps gives
-    the oracle's configuration (1e-12) and the same energies."""
+    the oracle's configuration (1e-12 per sweep) and the same energies.  With
+    a heat-bath sweep first the resident block does not load colour 0 (the
+    first half sweep redraws it); without one it loads the whole replica."""
     S, C, NT, seed = 2, 2, 3, 61
     res = {}
     for policy in ("resident", "streaming"):
@@ -342,7 +345,7 @@ def test_resident_and_streaming_paths_fp64(L):
         step0 = 4242
         eng.step = step0
         eng.profile(True)
-        eng.sweep(1, 3)
+        eng.sweep(n_hb, n_or)
         ms, n = eng.profile_read()
         assert (n["resident"] > 0) == (policy == "resident")
         out = get_state(eng, S, C, NT)
@@ -350,14 +353,16 @@ def test_resident_and_streaming_paths_fp64(L):
         for s in range(S):
             for c in range(C):
                 for b in range(NT):
-                    ref = _oracle_sweep(L, J[s], st[s, c, b], B[s, b], "hb", seed, s, c * NT + b, step0)
-                    for _ in range(3):
+                    ref = st[s, c, b]
+                    for k in range(n_hb):
+                        ref = _oracle_sweep(L, J[s], ref, B[s, b], "hb", seed, s, c * NT + b, step0 + 2 * k)
+                    for _ in range(n_or):
                         ref = _oracle_sweep(L, J[s], ref, B[s, b], "or", seed, s, 0, 0)
-                    # four sweeps: 1e-12 per sweep grows through the chaotic updates
+                    # several sweeps: 1e-12 per sweep grows through the chaotic updates
                     assert np.abs(out[s, c, b] - ref).max() <= 1e-11, (policy, s, c, b)
                     Hr = orc.energy(L, J[s], out[s, c, b])
                     assert abs(H[s, c, b] - Hr) <= 1e-11 * max(1, abs(Hr))
-        assert eng.step == step0 + 8
+        assert eng.step == step0 + 2 * (n_hb + n_or)
         res[policy] = out
         eng.close()
     assert np.abs(res["resident"] - res["streaming"]).max() <= 1e-14
