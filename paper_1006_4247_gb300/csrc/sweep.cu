@@ -163,6 +163,9 @@ __global__ void __launch_bounds__(TILE) k_overlap(DevBatch a) {
 #pragma unroll
         for (int n = 0; n < 9; ++n) part[n] = (T)0;
         const int end = min(NV, base + CH * TILE);
+        // two vectors of each copy in flight per thread (12 16-byte loads);
+        // the additions into part keep their order
+#pragma unroll 2
         for (int xv = base + (int)threadIdx.x; xv < end; xv += TILE) {
             const int x = xv * V;
             const int c = x >= half ? 1 : 0;
